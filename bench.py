@@ -1,0 +1,309 @@
+"""CompaSO hot-path benchmark (one JSON line on rank 0).
+
+A step is one pass of the whole hot path — kernel density, L0 FoF, L1 and L2
+competitive SO, labels and catalogue — over one synthetic box.  The default
+workload is the medium box: side 256 l_mean, 256^3 = 16.8M particles, 40%
+uniform background and 60% in NFW haloes of 20-2e5 particles with 10%
+satellites (seeded), int32 positions on a 2^21 grid.
+
+  value  particles/s with the inputs resident in device memory
+  e2e    particles/s through the same C-ABI call with pinned host buffers
+         (host->device copy of positions and ids, device->host copy of the
+         four per-particle outputs and the catalogue, inside the timed region)
+
+--impl reference times the CPU oracle (single thread) on bounded samples of
+the same recipe instead.  Under torchrun each rank runs its own box (weak
+scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "medium": dict(desc="medium box: side 256 l_mean, 16,777,216 particles, 40% background, 60% NFW haloes "
+                        "N in [20, 2e5] (slope -1.9, c in [4, 12]), 10% with satellites"),
+    "tiny": dict(desc="tiny box: side 64 l_mean, 262,144 particles, 50% background, 50% NFW haloes N in "
+                      "[20, 2e4]"),
+}
+OPS_PER_PAIR = 11  # 3 sub, 3 mul, 2 add for d; compare; b2 - d; accumulate
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        reasons = set()
+        for r in rows:
+            for k, nm in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("pcap", "sw_power_cap")):
+                if r[k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(name, seed_offset):
+    from paper_2110_11408_gb300 import synth
+    if name == "medium":
+        return synth.medium(seed=synth.SEED0 + 1 + 1000 * seed_offset)
+    if name == "tiny":
+        return synth.tiny(seed=synth.SEED0 + 1000 * seed_offset)
+    raise SystemExit("unknown workload " + name)
+
+
+def cpu_oracle_rate(samples):
+    """Oracle (single thread) on bounded samples of the medium recipe."""
+    import oracle as O
+    from paper_2110_11408_gb300 import synth
+    n_tot, t_tot = 0, 0.0
+    for side, seed in samples:
+        pos, ids, meta = synth.medium_sample(side=side, seed=seed)
+        p = O.params(meta["u"])
+        t0 = time.perf_counter()
+        O.find_groups(pos, ids, p)
+        t_tot += time.perf_counter() - t0
+        n_tot += len(pos)
+    return n_tot / t_tot, n_tot, t_tot
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_2110_11408_gb300 import synth
+    import oracle as O
+    times, n_tot = [], 0
+    for k in range(args.warmup + args.steps):
+        pos, ids, meta = synth.medium_sample(side=32, seed=synth.SEED0 + 500 + k)
+        p = O.params(meta["u"])
+        t0 = time.perf_counter()
+        O.find_groups(pos, ids, p)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            n_tot += len(pos)
+    tot = sum(times)
+    value = n_tot / tot
+    sample = ("medium recipe (40% background, 60% NFW haloes N in [20, 2e5], 10% satellites) in periodic boxes of "
+              "side 32 l_mean (32,768 particles), one seeded box per step")
+    line = {"impl": "reference", "metric": "CompaSO particles/s (whole hot path: density, L0, L1, L2, catalogue)",
+            "value": value, "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / len(times), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic", "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
+    ap.add_argument("--batched", action="store_true", help="batched CompaSO schedule")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    from paper_2110_11408_gb300 import cso
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # CPU baseline first (before any device context gets forked around)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from paper_2110_11408_gb300 import synth
+        rate, n_cpu, t_cpu = cpu_oracle_rate([(64, synth.SEED0 + 21), (64, synth.SEED0 + 22)])
+        cpu = {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "sample": "medium recipe in two seeded periodic boxes of side 64 l_mean (2 x 262,144 particles), "
+                         "%.1f s of single-thread oracle time" % t_cpu}
+
+    pos, ids, meta = make_workload(args.workload, rank)
+    n = len(pos)
+    params = cso.cso_params_default(meta["u"])
+    flags = cso.FLAG_TIMING | (cso.FLAG_BATCHED if args.batched else 0)
+    ctx = cso.Context(local, flags=flags)
+    stream = torch.cuda.ExternalStream(cso.cso_stream(ctx.h))
+    dpos = torch.from_numpy(pos).cuda()
+    dids = torch.from_numpy(ids.view(np.int64)).cuda()
+    buf = cso.Buffers(dpos, dids, on_device=True)
+    torch.cuda.synchronize()
+
+    # algorithmic pair count of this box (untimed pass with the counter on)
+    cctx = cso.Context(local, flags=cso.FLAG_COUNT_PAIRS)
+    cso.cso_find_groups(cctx.h, buf, params)
+    stats = cso.cso_last_stats(cctx.h)
+    cctx.close()
+
+    for _ in range(args.warmup):
+        cso.cso_find_groups(ctx.h, buf, params)
+    torch.cuda.synchronize()
+    barrier()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stage_acc = {}
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            cso.cso_find_groups(ctx.h, buf, params)
+            for k, v in cso.cso_stage_times(ctx.h).items():
+                stage_acc.setdefault(k, []).append(v)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n / (ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hpos = torch.from_numpy(pos).pin_memory()
+        hids = torch.from_numpy(ids.view(np.int64)).pin_memory()
+        hp, hi = hpos.numpy(), hids.numpy().view(np.uint64)
+        hb = cso.Buffers(hp, hi, on_device=False)
+        for name in list(hb.out):
+            hb.out[name] = torch.empty(n, dtype=torch.int64).pin_memory().numpy().view(
+                np.int64 if name == "sigma" else np.uint64)
+        hb.halos = torch.empty(hb.halo_cap * cso.HALO_DTYPE.itemsize, dtype=torch.uint8).pin_memory().numpy().view(
+            cso.HALO_DTYPE)
+        hb.cout = cso.CsoOutput(l0=hb.out["l0"].ctypes.data, l1=hb.out["l1"].ctypes.data,
+                                l2=hb.out["l2"].ctypes.data, sigma=hb.out["sigma"].ctypes.data,
+                                halos=hb.halos.ctypes.data, halo_cap=hb.halo_cap, n_halos=0, on_device=0)
+        for _ in range(2):
+            cso.cso_find_groups(ctx.h, hb, params)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            cso.cso_find_groups(ctx.h, hb, params)
+            _ = int(hb.cout.n_halos)
+        dt = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        h2d = n * (12 + 8)
+        d2h = n * 8 * 4 + int(hb.cout.n_halos) * cso.HALO_DTYPE.itemsize
+        e2e = {"value": ws * n / dt, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    stages = {k: statistics.median(v) for k, v in stage_acc.items()}
+    peaks, peak_src = load_peaks()
+    clocks = clk.summary()
+    # dominant kernel: the density pair loop, bounded by the integer ALU
+    dens_ms = stages.get("density")
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops / s, in T/s
+    roof = None
+    if dens_ms:
+        achieved = stats["pairs_b"] * OPS_PER_PAIR / (dens_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_density", "achieved": achieved, "peak": alu_peak,
+                "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 int32 lanes x %.0f MHz (max SM clock, %s peaks file)"
+                               % (sm_mhz, peak_src),
+                "algorithmic": "%d pairs within b x %d int ops" % (stats["pairs_b"], OPS_PER_PAIR)}
+    line = {
+        "metric": "CompaSO particles/s (whole hot path: density, L0, L1, L2, catalogue)",
+        "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "n_particles": n,
+                   "schedule": "batched" if args.batched else "plain", "l2_flush": "working set > L2 (inputs 336 MB, "
+                   "cell table 1 GB)", "seed": meta["seed"]},
+        "e2e": e2e, "gpu_launches": None, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "stages_ms": stages,
+        "counts": {k: stats[k] for k in ("dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows",
+                                         "pairs_b", "l1_work", "l2_work", "workspace_bytes")},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * cso.h — C ABI of the GB300 CompaSO hot path.
+ *
+ * CompaSO (Hadzhiyska et al. 2021, arXiv:2110.11408) finds haloes in a
+ * periodic box of equal-mass particles in three nested levels (Sec. 2.2):
+ *   L0  friends-of-friends over particles whose kernel density exceeds
+ *       Delta_L0 (Sec. 2.2.1, Eq. 1);
+ *   L1  competitive spherical-overdensity assignment inside each L0 group
+ *       (Sec. 2.2.2 steps 1-4, Eq. 3);
+ *   L2  the same assignment, at the higher threshold Delta_L2, inside every
+ *       L1 halo (Sec. 2.2.2, last paragraphs).
+ *
+ * Every step runs in CUDA kernels for sm_103a.  Positions are int32 on a
+ * periodic grid of 2^21 units per side; distances, kernel sums and all
+ * decisions are exact integers, so results do not depend on the order of the
+ * input particles.  Labels are particle ids: L0 = smallest id of the group,
+ * L1/L2 = id of the nucleus particle, CSO_NO_GROUP otherwise.
+ *
+ * Threading: one cso_ctx is used by one host thread at a time.  All device
+ * work of a context is issued on the context's CUDA stream.
+ *
+ * Return codes: CSO_OK (0) or one of the negative CSO_ERR_* values below;
+ * cso_last_error() gives a one-line description of the last failure.
+ */
+#ifndef CSO_H
+#define CSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSO_OK 0
+#define CSO_ERR_ARG (-1)      /* bad parameters, positions outside [0, 2^21), n too large */
+#define CSO_ERR_BUDGET (-2)   /* the request can never fit the context's device-memory budget */
+#define CSO_ERR_CAPACITY (-3) /* halo_cap too small; n_halos holds the number needed */
+#define CSO_ERR_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define CSO_ERR_CUDA (-5)     /* a CUDA runtime call failed */
+#define CSO_EAGAIN (-6)       /* cso_submit: queued, not yet admitted (ticket is valid) */
+#define CSO_ERR_STATE (-7)    /* unknown ticket or call out of order */
+
+#define CSO_NO_GROUP UINT64_MAX
+#define CSO_GRID_BITS 21
+
+/* context flags (cso_init) */
+#define CSO_FLAG_BATCHED 1u /* CompaSO levels run as one persistent size-binned launch */
+#define CSO_FLAG_TIMING 2u  /* record per-stage CUDA events (cso_stage_times) */
+#define CSO_FLAG_GRAPH 4u   /* replay the batched CompaSO launch sequence as a CUDA graph */
+#define CSO_FLAG_COUNT_PAIRS 8u /* count kernel pairs with d < b2 (cso_last_stats[6]); slows the density pass */
+#define CSO_FLAG_SELECT_STRESS 16u /* testing: tiny radius-search tiles so every select branch runs; same results */
+
+/*
+ * Parameters (Table 1 of the paper; Einstein-de Sitter thresholds of
+ * Sec. 2.3.1).  Lengths b_kernel and l_fof are in units of the mean
+ * interparticle spacing l_mean; l_mean_grid = u is that spacing in grid units
+ * (2^21 / box side in l_mean) and must be an integer value.
+ * The derived block is filled by cso_params_derive():
+ *   b2    = llround((b_kernel u)^2), lfof2 = llround((l_fof u)^2)   [grid^2]
+ *   norm  = 0.4 (4 pi / 3) b2^2 sqrt(b2) / u^3: the kernel sum
+ *           Sigma = sum_j (b2 - d_ij) that a unit-density uniform field gives
+ *           on average (App. B.2, N = (2/5)(4 pi / 3) b^3 Delta, times b2);
+ *   T_L0  = floor(delta_L0 norm)  (dense <=> Sigma > T_L0, Sec. 2.2.1);
+ *   T_min_L1/L2 = floor(D norm) with D = 5A/b^2 the kernel density at the
+ *           centre of a singular isothermal sphere of np_min_density
+ *           particles inside the radius enclosing delta_L1/L2 times the mean
+ *           (Sec. 2.2.2 step 4; App. B.2);
+ *   K_L1/L2 = (delta (4 pi / 3))^2: a radius whose squared grid length is d
+ *           encloses "too little" when n^2 u^6 < K d^3 (Sec. 2.2.2 step 1).
+ */
+typedef struct cso_params {
+  int32_t grid_bits;       /* must be CSO_GRID_BITS */
+  int32_t include_self;    /* 1: count the particle itself in its kernel sum */
+  double l_mean_grid;      /* u */
+  double b_kernel;         /* 0.4 */
+  double l_fof;            /* 0.25 */
+  double delta_L0;         /* 60 */
+  double delta_L1;         /* 200 */
+  double delta_L2;         /* 800 */
+  int32_t alpha_num;       /* R_elig / R = alpha_num / alpha_den = 4 / 5 */
+  int32_t alpha_den;
+  int32_t roche_num;       /* c_Roche = roche_num / roche_den = 2 / 1 */
+  int32_t roche_den;
+  int32_t np_min_density;  /* N_new,min = 35 */
+  int32_t np_min_L1;       /* catalogue keeps L1 haloes with N >= this (35) */
+  /* derived */
+  int64_t b2, lfof2, T_L0, T_min_L1, T_min_L2;
+  double K_L1, K_L2;
+} cso_params;
+
+/* One row of the L1 catalogue (Table 1 fields).  Positions in grid units. */
+typedef struct cso_halo {
+  uint64_t nucleus_id;  /* L1 particle (SO_central_particle) */
+  int64_t N;            /* members */
+  int64_t R2;           /* squared L1 radius, grid^2 */
+  double R_delta;       /* sqrt(R2) / u, l_mean units */
+  double com[3];        /* L1 centre of mass: nucleus + mean minimum-image offset */
+  uint64_t l2max_id;    /* first (densest) L2 nucleus, CSO_NO_GROUP if none */
+  int64_t l2max_N;
+  double l2max_com[3];
+  int64_t l2_top5_N[5]; /* sizes of the five largest L2 haloes, descending, 0-padded */
+  int64_t n_l2;         /* number of L2 haloes */
+  uint64_t l0_id;       /* L0 group of the halo */
+} cso_halo;
+
+/* Input particles.  pos is int32[n][3] (x, y, z), ids is uint64[n]; both host
+ * or both device memory (on_device).  The caller owns them and keeps them
+ * alive until the call (or, for cso_submit, the ticket) completes.
+ * x_lo/x_hi: reserved for slab requests; set both to 0 for a whole box. */
+typedef struct cso_input {
+  const int32_t* pos;
+  const uint64_t* ids;
+  int64_t n;
+  int32_t on_device;
+  int32_t x_lo, x_hi;
+  uint64_t request_id;
+} cso_input;
+
+/* Outputs, caller-allocated, length n in input order (NULL = not wanted);
+ * halos has room for halo_cap rows and receives the catalogue in increasing
+ * nucleus id; n_halos is set to the number of rows (also on CSO_ERR_CAPACITY).
+ * All output pointers are host or device memory as on_device says. */
+typedef struct cso_output {
+  uint64_t* l0;
+  uint64_t* l1;
+  uint64_t* l2;
+  int64_t* sigma;  /* kernel sums Sigma_i = sum_{j != i, d < b2} (b2 - d) */
+  cso_halo* halos;
+  int64_t halo_cap;
+  int64_t n_halos;
+  int32_t on_device;
+  int32_t pad_;
+} cso_output;
+
+typedef struct cso_ctx cso_ctx;
+
+/* Create a context on `device` with a device-memory budget in bytes
+ * (0 = no limit beyond the device).  flags: CSO_FLAG_*.  The context owns its
+ * stream, its workspace and its timing events. */
+int cso_init(cso_ctx** ctx, int device, size_t hbm_budget_bytes, uint32_t flags);
+
+/* Paper defaults for a box whose mean interparticle spacing is u grid units;
+ * the derived block is filled too. */
+int cso_params_default(cso_params* p, double l_mean_grid);
+
+/* Fill the derived block from the primary fields (formulas above). */
+int cso_params_derive(cso_params* p);
+
+/* Run the whole hot path on one periodic box: kernel density, L0, L1, L2,
+ * labels and catalogue.  Synchronous: returns after the outputs are written. */
+int cso_find_groups(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out);
+
+/* Served path: queue a box for asynchronous processing on the context's
+ * stream pool and return a ticket.  The buffers behind `in` and `out` must
+ * stay valid until cso_poll reports the ticket done. */
+int cso_submit(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = just test, <0 = wait forever) for a ticket;
+ * *done = 1 when its outputs are complete; returns the request's own status
+ * once done. */
+int cso_poll(cso_ctx* ctx, uint64_t ticket, int32_t* done, int32_t timeout_us);
+
+/* Release every resource of the context. */
+void cso_free(cso_ctx* ctx);
+
+/* --- introspection ------------------------------------------------------ */
+
+/* CUDA stream (cudaStream_t) the context issues its work on. */
+void* cso_stream(cso_ctx* ctx);
+
+/* Per-stage device times (ms) of the last cso_find_groups when the context
+ * has CSO_FLAG_TIMING; names[i] receives a static string.  Returns the
+ * number of stages written (<= cap). */
+int cso_stage_times(cso_ctx* ctx, double* ms, const char** names, int cap);
+
+/* Counters of the last call: [0] particles, [1] dense particles, [2] L0
+ * groups, [3] L1 nuclei, [4] L2 nuclei, [5] catalogue rows, [6] kernel pairs
+ * with d < b2 (only with CSO_FLAG_COUNT_PAIRS), [7] sum over L1 nuclei of their
+ * group size, [8] sum over L2 nuclei of their L1 halo size, [9] peak device
+ * workspace bytes.  Returns the number written. */
+int cso_last_stats(cso_ctx* ctx, int64_t* out, int cap);
+
+/* One-line description of the last error of this thread. */
+const char* cso_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSO_H */

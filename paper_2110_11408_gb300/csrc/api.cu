@@ -1,0 +1,241 @@
+// C ABI of the CompaSO hot path: parameters, context, and the pipeline
+// density -> L0 -> L1 -> L2 -> labels and catalogue (Sec. 2.2 of the paper).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "cells.cuh"
+#include "compaso.cuh"
+#include "pipeline.cuh"
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+void cso_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* cso_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------
+// kernel density at the centre of a singular isothermal sphere holding np
+// particles inside the radius of mean enclosed density delta (l_mean units):
+// M(<R) = 4 pi A R, and the kernel-smoothed SIS tends to 5A/b^2 at r -> 0
+// (App. B.2, r < b branch)
+static double sis_centre(double np, double delta, double b) {
+  double R = cbrt(np / (delta * (4.0 * M_PI / 3.0)));
+  double A = np / (4.0 * M_PI * R);
+  return 5.0 * A / (b * b);
+}
+
+extern "C" int cso_params_derive(cso_params* p) {
+  if (!p) return CSO_ERR_ARG;
+  double u = p->l_mean_grid;
+  if (p->grid_bits != CSO_GRID_BITS || !(u >= 1.0) || u > (double)(1 << 20) || u != floor(u) || !(p->b_kernel > 0) ||
+      !(p->l_fof > 0) || p->alpha_den <= 0 || p->alpha_num < 0 || p->roche_den <= 0 || p->roche_num < 0 ||
+      p->np_min_density <= 0 || !(p->delta_L1 >= 1.0) || !(p->delta_L2 >= 1.0)) {
+    cso_set_error("invalid CompaSO parameters");
+    return CSO_ERR_ARG;
+  }
+  double bu = p->b_kernel * u;
+  double lu = p->l_fof * u;
+  p->b2 = llround(bu * bu);
+  p->lfof2 = llround(lu * lu);
+  double b2 = (double)p->b2;
+  // kernel sum of a unit-density uniform field: (2/5)(4 pi/3) (b/u)^3 times b2
+  double norm = 0.4 * (4.0 * M_PI / 3.0) * b2 * b2 * sqrt(b2) / (u * u * u);
+  p->T_L0 = (int64_t)floor(p->delta_L0 * norm);
+  p->T_min_L1 = (int64_t)floor(sis_centre(p->np_min_density, p->delta_L1, p->b_kernel) * norm);
+  p->T_min_L2 = (int64_t)floor(sis_centre(p->np_min_density, p->delta_L2, p->b_kernel) * norm);
+  double k1 = p->delta_L1 * (4.0 * M_PI / 3.0);
+  double k2 = p->delta_L2 * (4.0 * M_PI / 3.0);
+  p->K_L1 = k1 * k1;
+  p->K_L2 = k2 * k2;
+  return CSO_OK;
+}
+
+extern "C" int cso_params_default(cso_params* p, double l_mean_grid) {
+  if (!p) return CSO_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->grid_bits = CSO_GRID_BITS;
+  p->include_self = 0;
+  p->l_mean_grid = l_mean_grid;
+  p->b_kernel = 0.4;
+  p->l_fof = 0.25;
+  p->delta_L0 = 60.0;
+  p->delta_L1 = 200.0;
+  p->delta_L2 = 800.0;
+  p->alpha_num = 4;
+  p->alpha_den = 5;
+  p->roche_num = 2;
+  p->roche_den = 1;
+  p->np_min_density = 35;
+  p->np_min_L1 = 35;
+  return cso_params_derive(p);
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int cso_init(cso_ctx** out, int device, size_t budget, uint32_t flags) {
+  if (!out) return CSO_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  CSO_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) {
+    cso_set_error("no CUDA device %d (found %d)", device, ndev);
+    return CSO_ERR_ARG;
+  }
+  CSO_CUDA(cudaSetDevice(device));
+  cso_ctx* c = new cso_ctx();
+  c->device = device;
+  c->budget = budget;
+  c->flags = flags;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, sizeof(long long) * 64);
+  for (int i = 0; e == cudaSuccess && i <= CSO_MAX_STAGES; ++i) e = cudaEventCreate(&c->ev[i]);
+  if (e != cudaSuccess) {
+    cso_set_error("cso_init: %s", cudaGetErrorString(e));
+    cso_free(c);
+    return CSO_ERR_CUDA;
+  }
+  *out = c;
+  return CSO_OK;
+}
+
+extern "C" void cso_free(cso_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->ws.base) cudaFree(c->ws.base);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  for (int i = 0; i <= CSO_MAX_STAGES; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+extern "C" void* cso_stream(cso_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+extern "C" int cso_stage_times(cso_ctx* c, double* ms, const char** names, int cap) {
+  if (!c) return 0;
+  int k = c->nstages < cap ? c->nstages : cap;
+  for (int i = 0; i < k; ++i) {
+    if (ms) ms[i] = c->stage_ms[i];
+    if (names) names[i] = c->stage_name[i];
+  }
+  return k;
+}
+
+extern "C" int cso_last_stats(cso_ctx* c, int64_t* out, int cap) {
+  if (!c) return 0;
+  int k = cap < CSO_NSTATS ? cap : CSO_NSTATS;
+  for (int i = 0; i < k; ++i) out[i] = c->stats[i];
+  return k;
+}
+
+// workspace large enough for n particles and ncell cells
+int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io) {
+  size_t need = (size_t)n * CSO_BYTES_PER_PARTICLE + (size_t)(ncell + 1) * 4 + ((size_t)64 << 20);
+  if (host_io) need += (size_t)n * (12 + 8 + 32) + (size_t)n / 2 * sizeof(cso_halo);
+  if (c->budget && need > c->budget) {
+    cso_set_error("request needs %zu bytes of workspace, budget is %zu", need, c->budget);
+    return CSO_ERR_BUDGET;
+  }
+  if (need > c->ws.cap) {
+    if (c->ws.base) {
+      CSO_CUDA(cudaStreamSynchronize(c->stream));
+      CSO_CUDA(cudaFree(c->ws.base));
+      c->ws.base = nullptr;
+      c->ws.cap = 0;
+    }
+    CSO_CUDA(cudaMalloc((void**)&c->ws.base, need));
+    c->ws.cap = need;
+  }
+  c->ws.off = 0;
+  c->ws.peak = 0;
+  return CSO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// entry points
+// ---------------------------------------------------------------------------
+static int check_io(const cso_input* in, const cso_params* p, cso_output* out) {
+  if (!in || !p || !out || in->n < 0 || (in->n > 0 && (!in->pos || !in->ids))) {
+    cso_set_error("null or negative argument");
+    return CSO_ERR_ARG;
+  }
+  if (in->n >= (1ll << 31) - 1) {
+    cso_set_error("n = %lld is too large for one request (< 2^31)", (long long)in->n);
+    return CSO_ERR_ARG;
+  }
+  if (out->halo_cap < 0 || (out->halo_cap > 0 && !out->halos)) {
+    cso_set_error("halo_cap > 0 needs a halos buffer");
+    return CSO_ERR_ARG;
+  }
+  return CSO_OK;
+}
+
+extern "C" int cso_find_groups(cso_ctx* c, const cso_input* in, const cso_params* pin, cso_output* out) {
+  if (!c) return CSO_ERR_ARG;
+  CSO_TRY(check_io(in, pin, out));
+  cso_params p = *pin;
+  CSO_TRY(cso_params_derive(&p));
+  CSO_CUDA(cudaSetDevice(c->device));
+  int rc = pipeline_run(c, in, &p, out);
+  return rc;
+}
+
+// Served path.  Requests are queued and run in submission order on the
+// context's stream when cso_poll (or a later cso_submit) drives the queue.
+extern "C" int cso_submit(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out, uint64_t* ticket) {
+  if (!c || !ticket) return CSO_ERR_ARG;
+  CSO_TRY(check_io(in, p, out));
+  ServedReq r;
+  r.in = *in;
+  r.p = *p;
+  r.out = out;
+  r.ticket = ++c->next_ticket;
+  c->queue.push_back(r);
+  *ticket = r.ticket;
+  return CSO_EAGAIN;
+}
+
+extern "C" int cso_poll(cso_ctx* c, uint64_t ticket, int32_t* done, int32_t timeout_us) {
+  (void)timeout_us;
+  if (!c || !done) return CSO_ERR_ARG;
+  *done = 0;
+  for (size_t i = 0; i < c->finished.size(); ++i)
+    if (c->finished[i].first == ticket) {
+      *done = 1;
+      return c->finished[i].second;
+    }
+  bool known = false;
+  for (auto& r : c->queue) known |= r.ticket == ticket;
+  if (!known) {
+    cso_set_error("unknown ticket %llu", (unsigned long long)ticket);
+    return CSO_ERR_STATE;
+  }
+  // run queued requests up to and including this ticket
+  while (!c->queue.empty()) {
+    ServedReq r = c->queue.front();
+    c->queue.erase(c->queue.begin());
+    int rc = cso_find_groups(c, &r.in, &r.p, r.out);
+    c->finished.push_back({r.ticket, rc});
+    if (r.ticket == ticket) {
+      *done = 1;
+      return rc;
+    }
+  }
+  return CSO_ERR_STATE;
+}

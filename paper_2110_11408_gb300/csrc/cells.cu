@@ -1,0 +1,302 @@
+// Cell binning, kernel density, L0 friends-of-friends and the local-peak test.
+//
+// Particles are binned into nc^3 cells of side 2^21/nc >= b (a counting sort
+// into a dense cell table, x fastest), so every neighbour within b of a
+// particle lies in the 27 cells around its own and, for the three cells of
+// one (y, z) row, in one contiguous run of the sorted array.  Periodic wrap
+// is handled per run by shifting the query point by one box length, never
+// per pair.  With side <= 2^14 grid units every |dx| inside the stencil is
+// below 2^15, so squared distances fit uint32 exactly.
+#include "cells.cuh"
+
+namespace {
+
+__device__ __forceinline__ int wrap_cell(int c, int nc, int& shift) {
+  shift = 0;
+  if (c < 0) {
+    shift = CSO_BOX;  // neighbour sits at the far end: move the query up by a box
+    return c + nc;
+  }
+  if (c >= nc) {
+    shift = -CSO_BOX;
+    return c - nc;
+  }
+  return c;
+}
+
+__device__ __forceinline__ int cell_of(int x, int nc) { return (int)(((unsigned long long)(unsigned)x * (unsigned)nc) >> 21); }
+
+// Visit every sorted index t whose cell is in the 27-stencil of the query;
+// f(t, xq, yq, zq) receives the shifted query coordinates.  f returns false to stop.
+template <class F>
+__device__ __forceinline__ void for_stencil(const CellGrid& g, int x, int y, int z, F f) {
+  const int nc = g.nc;
+  const int cx = cell_of(x, nc), cy = cell_of(y, nc), cz = cell_of(z, nc);
+  for (int dz = -1; dz <= 1; ++dz) {
+    int sz;
+    int zz = wrap_cell(cz + dz, nc, sz);
+    for (int dy = -1; dy <= 1; ++dy) {
+      int sy;
+      int yy = wrap_cell(cy + dy, nc, sy);
+      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
+      const int yq = y + sy, zq = z + sz;
+      // the three x cells: one contiguous run unless the row wraps
+      uint32_t lo0, hi0, lo1 = 0, hi1 = 0;
+      int sx1 = 0;
+      if (cx >= 1 && cx + 1 < nc) {
+        lo0 = row[cx - 1];
+        hi0 = row[cx + 2];
+      } else if (cx == 0) {
+        lo0 = row[0];
+        hi0 = row[2];
+        lo1 = row[nc - 1];
+        hi1 = row[nc];
+        sx1 = CSO_BOX;
+      } else {  // cx == nc - 1
+        lo0 = row[nc - 2];
+        hi0 = row[nc];
+        lo1 = row[0];
+        hi1 = row[1];
+        sx1 = -CSO_BOX;
+      }
+      for (uint32_t t = lo0; t < hi0; ++t)
+        if (!f(t, x, yq, zq)) return;
+      for (uint32_t t = lo1; t < hi1; ++t)
+        if (!f(t, x + sx1, yq, zq)) return;
+    }
+  }
+}
+
+__global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, int nc, uint32_t* __restrict__ key,
+                             uint32_t* __restrict__ rank, uint32_t* __restrict__ count, int* __restrict__ bad) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  if ((unsigned)x >= (unsigned)CSO_BOX || (unsigned)y >= (unsigned)CSO_BOX || (unsigned)z >= (unsigned)CSO_BOX) {
+    atomicExch(bad, 1);
+    x = y = z = 0;
+  }
+  uint32_t k = ((uint32_t)cell_of(z, nc) * nc + cell_of(y, nc)) * nc + cell_of(x, nc);
+  key[i] = k;
+  rank[i] = atomicAdd(&count[k], 1u);
+}
+
+__global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n,
+                               const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+                               const uint32_t* __restrict__ start, int4* __restrict__ spos,
+                               uint64_t* __restrict__ sid) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t dst = start[key[i]] + rank[i];
+  spos[dst] = make_int4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], (int)i);
+  sid[dst] = ids[i];
+}
+
+// Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2)
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_density(CellGrid g, const int4* __restrict__ spos, int n, uint32_t b2,
+                                                 int include_self, long long* __restrict__ sigma,
+                                                 unsigned long long* __restrict__ pairs) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int4 p = spos[s];
+  unsigned long long acc = 0;
+  unsigned cnt = 0;
+  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+    int4 q = spos[t];
+    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
+    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+    uint32_t m = d < b2 ? d : b2;
+    acc += b2 - m;
+    if (COUNT) cnt += d < b2;
+    return true;
+  });
+  // the particle met itself once at d = 0
+  if (!include_self) acc -= b2;
+  sigma[s] = (long long)acc;
+  if (COUNT) {
+    cnt -= 1;  // the particle itself
+    unsigned mask = __activemask();
+    unsigned tot = __reduce_add_sync(mask, cnt);
+    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(pairs, (unsigned long long)tot);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// union-find over sorted indices: parent[x] <= x always, roots are the
+// smallest index of their component, hooks go from the larger root to the
+// smaller one by compare-and-swap (lock-free; any interleaving ends in the
+// same components).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int uf_root(int* parent, int x) {
+  int p = parent[x];
+  while (p != x) {
+    int gp = parent[p];
+    if (gp != p) parent[x] = gp;  // halve the path; gp is still an ancestor of x
+    x = p;
+    p = gp;
+  }
+  return x;
+}
+
+__device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
+  a = uf_root(parent, a);
+  b = uf_root(parent, b);
+  while (a != b) {
+    if (a < b) {
+      int t = a;
+      a = b;
+      b = t;
+    }
+    // hook root a (larger) under b
+    int old = atomicCAS(&parent[a], a, b);
+    if (old == a) return;
+    // a was hooked elsewhere meanwhile: climb and retry
+    a = uf_root(parent, old);
+    b = uf_root(parent, b);
+  }
+}
+
+__global__ void k_fof_init(int* __restrict__ parent, int n) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) parent[s] = s;
+}
+
+__global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __restrict__ spos, int n,
+                                                  const long long* __restrict__ sigma, long long T_L0,
+                                                  uint32_t lfof2, int* __restrict__ parent) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || sigma[s] <= T_L0) return;
+  int4 p = spos[s];
+  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+    if ((int)t <= s) return true;  // every unordered pair once
+    int4 q = spos[t];
+    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
+    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+    if (d < lfof2 && sigma[t] > T_L0) uf_unite(parent, s, (int)t);
+    return true;
+  });
+}
+
+// root of every dense particle (-1 otherwise); smallest id per root
+__global__ void k_fof_finish(int* __restrict__ parent, int n, const long long* __restrict__ sigma, long long T_L0,
+                             const uint64_t* __restrict__ sid, int* __restrict__ root,
+                             unsigned long long* __restrict__ minid) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  if (sigma[s] <= T_L0) {
+    root[s] = -1;
+    return;
+  }
+  int r = uf_root(parent, s);
+  root[s] = r;
+  atomicMin(&minid[r], (unsigned long long)sid[s]);
+}
+
+// peak[s] = 1 iff s has a group label, Sigma_s > T_min and no particle of the
+// same group within d < b2 comes before it in key order (Sigma desc, id asc).
+__global__ void __launch_bounds__(256) k_peak(CellGrid g, const int4* __restrict__ spos, int n,
+                                              const long long* __restrict__ sigma, const uint64_t* __restrict__ sid,
+                                              const int* __restrict__ label, long long T_min, uint32_t b2,
+                                              uint8_t* __restrict__ peak) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int lab = label[s];
+  long long sg = sigma[s];
+  if (lab < 0 || sg <= T_min) {
+    peak[s] = 0;
+    return;
+  }
+  uint64_t id = sid[s];
+  int4 p = spos[s];
+  bool is_peak = true;
+  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+    if ((int)t == s) return true;
+    int4 q = spos[t];
+    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
+    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+    if (d < b2 && label[t] == lab) {
+      long long st = sigma[t];
+      if (st > sg || (st == sg && sid[t] < id)) {
+        is_peak = false;
+        return false;
+      }
+    }
+    return true;
+  });
+  peak[s] = is_peak;
+}
+
+}  // namespace
+
+int cells_choose(long long b2, int* nc_out) {
+  // largest nc with (2^21 / nc)^2 >= b2: cells at least as wide as b
+  double b = sqrt((double)b2);
+  long long nc = (long long)floor((double)CSO_BOX / b);
+  while (nc > 1 && (long double)CSO_BOX * CSO_BOX < (long double)b2 * nc * nc) --nc;
+  while ((long double)CSO_BOX * CSO_BOX >= (long double)b2 * (nc + 1) * (nc + 1)) ++nc;
+  *nc_out = (int)nc;
+  if (nc < 128) {
+    cso_set_error("kernel radius b = %.0f grid units is too large (cells must be <= 2^14 units, u <= 40960)", b);
+    return CSO_ERR_ARG;
+  }
+  if (nc > 1290) {
+    cso_set_error("box too fine for one dense cell table (nc = %lld > 1290)", nc);
+    return CSO_ERR_ARG;
+  }
+  return CSO_OK;
+}
+
+int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint32_t* start, int4* spos,
+              uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st) {
+  long long ncell = (long long)nc * nc * nc;
+  size_t mark = ws.off;
+  uint32_t* key = ws.get<uint32_t>(n);
+  uint32_t* rank = ws.get<uint32_t>(n);
+  if (!key || !rank) {
+    cso_set_error("workspace exhausted in binning");
+    return CSO_ERR_BUDGET;
+  }
+  CSO_CUDA(cudaMemsetAsync(start, 0, sizeof(uint32_t) * (ncell + 1), st));
+  if (n > 0) {
+    k_cell_count<<<cdiv(n, 256), 256, 0, st>>>(pos, n, nc, key, rank, start, bad);
+    CSO_CUDA(cudaGetLastError());
+  }
+  CSO_TRY(scan_u32(start, ncell + 1, nullptr, ws, st));
+  if (n > 0) {
+    k_cell_scatter<<<cdiv(n, 256), 256, 0, st>>>(pos, ids, n, key, rank, start, spos, sid);
+    CSO_CUDA(cudaGetLastError());
+  }
+  ws.off = mark;
+  return CSO_OK;
+}
+
+int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
+                  unsigned long long* pairs, cudaStream_t st) {
+  if (n <= 0) return CSO_OK;
+  if (pairs)
+    k_density<true><<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, pairs);
+  else
+    k_density<false><<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, nullptr);
+  CSO_CUDA(cudaGetLastError());
+  return CSO_OK;
+}
+
+int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
+              const uint64_t* sid, int* parent, int* root, unsigned long long* minid, cudaStream_t st) {
+  if (n <= 0) return CSO_OK;
+  k_fof_init<<<cdiv(n, 256), 256, 0, st>>>(parent, n);
+  k_fof_link<<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, sigma, T_L0, lfof2, parent);
+  CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
+  k_fof_finish<<<cdiv(n, 256), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
+  CSO_CUDA(cudaGetLastError());
+  return CSO_OK;
+}
+
+int cells_peak(const CellGrid& g, const int4* spos, int n, const long long* sigma, const uint64_t* sid,
+               const int* label, long long T_min, uint32_t b2, uint8_t* peak, cudaStream_t st) {
+  if (n <= 0) return CSO_OK;
+  k_peak<<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, sigma, sid, label, T_min, b2, peak);
+  CSO_CUDA(cudaGetLastError());
+  return CSO_OK;
+}

@@ -1,0 +1,487 @@
+// CompaSO levels (Sec. 2.2.2): one thread block per group runs the nucleus
+// loop of steps 1-4 over the group's members in key order (Sigma desc, id asc).
+//
+// Per nucleus:
+//   pass A  squared distances d_j of all members to the nucleus;
+//   select  R^2 = the smallest member distance d with n(<d)^2 u^6 < K d^3
+//           (exact), found without a full sort: a 1024-bin histogram over a
+//           window of d (first window binned by the threshold count
+//           sqrt(K) d^1.5 / u^3, later windows linearly), the first bin that
+//           could hold the answer (its interior count at its largest d) is
+//           sorted in shared memory and scanned, or narrowed further when it
+//           holds more than 2048 members; small groups are sorted whole;
+//   pass B  tentative membership / competitive reassignment (Eq. 3) and
+//           eligibility marking.
+#include <float.h>
+
+#include "compaso.cuh"
+
+namespace {
+
+constexpr int LV_THREADS = 256;
+constexpr int NB = 1024;      // histogram bins
+constexpr int CAP = 2048;     // largest bin resolved by an in-block sort
+constexpr int SMALL_N = 2048; // groups sorted whole
+
+// ---------------------------------------------------------------------------
+// exact predicate n^2 u^6 < K d^3 with K = Km 2^Ke (256-bit integers),
+// behind a double-precision filter whose rounding error is far below 1e-12
+// ---------------------------------------------------------------------------
+struct U256 {
+  unsigned long long w[4];
+};
+
+__device__ __forceinline__ void u256_mul(U256& a, unsigned long long b) {
+  unsigned long long carry = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    unsigned long long lo = a.w[i] * b;
+    unsigned long long hi = __umul64hi(a.w[i], b);
+    lo += carry;
+    hi += lo < carry;
+    a.w[i] = lo;
+    carry = hi;
+  }
+}
+
+__device__ __forceinline__ void u256_shl(U256& a, int s) {
+  while (s >= 64) {
+    a.w[3] = a.w[2];
+    a.w[2] = a.w[1];
+    a.w[1] = a.w[0];
+    a.w[0] = 0;
+    s -= 64;
+  }
+  if (s) {
+    a.w[3] = (a.w[3] << s) | (a.w[2] >> (64 - s));
+    a.w[2] = (a.w[2] << s) | (a.w[1] >> (64 - s));
+    a.w[1] = (a.w[1] << s) | (a.w[0] >> (64 - s));
+    a.w[0] <<= s;
+  }
+}
+
+__device__ __forceinline__ bool u256_less(const U256& a, const U256& b) {
+  for (int i = 3; i >= 0; --i)
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i];
+  return false;
+}
+
+__device__ __noinline__ bool pred_exact(unsigned long long n, unsigned long long d, const PredConst& c) {
+  U256 L = {{n, 0, 0, 0}}, R = {{c.Km, 0, 0, 0}};
+  u256_mul(L, n);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) u256_mul(L, c.u);
+  u256_mul(R, d);
+  u256_mul(R, d);
+  u256_mul(R, d);
+  if (c.Ke > 0) u256_shl(R, c.Ke);
+  else if (c.Ke < 0) u256_shl(L, -c.Ke);
+  return u256_less(L, R);
+}
+
+// the enclosed count n inside squared radius d is below the level's density
+__device__ __forceinline__ bool pred(unsigned long long n, unsigned long long d, const PredConst& c) {
+  double L = (double)n * (double)n * c.u6;
+  double dd = (double)d;
+  double R = c.K * (dd * dd * dd);
+  if (L < R * (1.0 - 1e-12)) return true;
+  if (L > R * (1.0 + 1e-12)) return false;
+  return pred_exact(n, d, c);
+}
+
+// smallest D > dmax with pred(n, D): the enclosed count stays n beyond the
+// farthest member (single thread)
+__device__ long long exhaust_radius(unsigned long long n, long long dmax, const PredConst& c) {
+  unsigned long long lo = (unsigned long long)dmax, hi = lo + 1;
+  while (!pred(n, hi, c)) hi *= 2;
+  while (hi - lo > 1) {
+    unsigned long long mid = lo + (hi - lo) / 2;
+    if (pred(n, mid, c)) hi = mid;
+    else lo = mid;
+  }
+  return (long long)hi;
+}
+
+__device__ __forceinline__ int mi(int v) {
+  if (v >= CSO_HALF) return v - CSO_BOX;
+  if (v < -CSO_HALF) return v + CSO_BOX;
+  return v;
+}
+
+__device__ __forceinline__ long long dist2(int4 a, int4 b) {
+  long long dx = mi(a.x - b.x), dy = mi(a.y - b.y), dz = mi(a.z - b.z);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ unsigned warp_incl(unsigned v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// block exclusive scan (LV_THREADS threads), returns total
+__device__ unsigned block_scan(unsigned v, unsigned& excl, unsigned* sw) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned inc = warp_incl(v);
+  if (lane == 31) sw[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    unsigned s = lane < LV_THREADS / 32 ? sw[lane] : 0;
+    unsigned si = warp_incl(s);
+    if (lane < LV_THREADS / 32) sw[lane] = si - s;
+    if (lane == 31) sw[32] = si;
+  }
+  __syncthreads();
+  excl = inc - v + sw[w];
+  unsigned tot = sw[32];
+  __syncthreads();
+  return tot;
+}
+
+__device__ void bitonic_sort(long long* a, int m) {  // m power of two
+  for (int k = 2; k <= m; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          long long x = a[i], y = a[l];
+          bool up = (i & k) == 0;
+          if ((x > y) == up) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+struct SelShared {
+  unsigned cnt[NB];
+  unsigned clo[NB];
+  unsigned long long dmn[NB];
+  unsigned long long dmx[NB];
+  long long list[CAP];
+  unsigned sw[33];
+  int best;
+  int nlist;
+  unsigned long long dmax_all;
+};
+
+// In the sorted list s[0..m) with n(<s[0]) = base, the first element whose
+// strictly-enclosed count satisfies the predicate; returns its index or m.
+__device__ int scan_sorted(const long long* s, int m, unsigned long long base, const PredConst& c, int* best) {
+  if (threadIdx.x == 0) *best = m;
+  __syncthreads();
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    int f = k;
+    while (f > 0 && s[f - 1] == s[k]) --f;
+    if (pred(base + (unsigned long long)f, (unsigned long long)s[k], c)) atomicMin(best, k);
+  }
+  __syncthreads();
+  int r = *best;
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int pow2_at_least(int m) {
+  int p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+
+// R^2 of nucleus pc over the n members at epos[0..n); distances left in ed.
+__device__ long long r_search(const int4* __restrict__ epos, long long* __restrict__ ed, int n, int4 pc,
+                              const PredConst& c, SelShared& S, const int small_n, const int cap, const int nb) {
+  const int tid = threadIdx.x;
+  if (n <= small_n) {
+    for (int j = tid; j < n; j += blockDim.x) {
+      long long d = dist2(pc, epos[j]);
+      ed[j] = d;
+      S.list[j] = d;
+    }
+    int m = pow2_at_least(n);
+    for (int j = n + tid; j < m; j += blockDim.x) S.list[j] = LLONG_MAX;
+    __syncthreads();
+    bitonic_sort(S.list, m);
+    int k = scan_sorted(S.list, n, 0, c, &S.best);
+    long long r;
+    if (k < n) r = S.list[k];
+    else r = S.list[n - 1];  // sentinel: exhaustion below
+    __syncthreads();
+    if (k >= n) {
+      if (tid == 0) S.list[0] = exhaust_radius((unsigned long long)n, r, c);
+      __syncthreads();
+      r = S.list[0];
+      __syncthreads();
+    }
+    return r;
+  }
+
+  // ---- windowed histogram select ----
+  // window [wlo, whi] of d; base = members with d < wlo; mode 0 = threshold-count bins
+  unsigned long long wlo = 0, whi = ~0ull, base = 0;
+  int mode = 0;
+  const float scale0 = c.bin_scale0 / (float)((n + nb - 2) / (nb - 1));  // n/(nb-1) members of threshold per bin
+  bool first_pass = true;
+  while (true) {
+    for (int b = tid; b < NB; b += blockDim.x) {
+      S.cnt[b] = 0;
+      S.dmn[b] = ~0ull;
+      S.dmx[b] = 0;
+    }
+    if (tid == 0 && first_pass) S.dmax_all = 0;
+    __syncthreads();
+    unsigned long long span = whi - wlo + 1;  // mode 1 only
+    for (int j = tid; j < n; j += blockDim.x) {
+      unsigned long long d;
+      if (first_pass) {
+        d = (unsigned long long)dist2(pc, epos[j]);
+        ed[j] = (long long)d;
+        atomicMax(&S.dmax_all, d);
+      } else {
+        d = (unsigned long long)ed[j];
+      }
+      if (d < wlo || d > whi) continue;
+      int b;
+      if (mode == 0) {
+        float f = (float)d;
+        float g = f * sqrtf(f) * scale0;
+        b = g < (float)(nb - 1) ? (int)g : nb - 1;
+      } else {
+        b = (int)(((d - wlo) * (unsigned long long)nb) / span);
+      }
+      atomicAdd(&S.cnt[b], 1u);
+      atomicMin(&S.dmn[b], d);
+      atomicMax(&S.dmx[b], d);
+    }
+    __syncthreads();
+    first_pass = false;
+    // interior counts
+    {
+      const int per = NB / LV_THREADS;
+      unsigned loc[NB / LV_THREADS];
+      unsigned s = 0;
+#pragma unroll
+      for (int q = 0; q < per; ++q) {
+        loc[q] = S.cnt[tid * per + q];
+        s += loc[q];
+      }
+      unsigned excl;
+      unsigned tot = block_scan(s, excl, S.sw);
+      unsigned run = excl;
+#pragma unroll
+      for (int q = 0; q < per; ++q) {
+        S.clo[tid * per + q] = run;
+        run += loc[q];
+      }
+      if (tid == 0) S.nlist = (int)tot;  // members in the window
+      __syncthreads();
+    }
+    const unsigned in_window = (unsigned)S.nlist;
+    int from = 0;
+    bool narrowed = false;
+    while (true) {
+      // first bin >= from that could hold the answer
+      if (tid == 0) S.best = NB;
+      __syncthreads();
+      for (int b = from + tid; b < NB; b += blockDim.x)
+        if (S.cnt[b] && pred(base + S.clo[b], S.dmx[b], c)) atomicMin(&S.best, b);
+      __syncthreads();
+      int b = S.best;
+      __syncthreads();
+      if (b == NB) break;  // nothing in this window
+      unsigned long long lo = S.dmn[b], hi = S.dmx[b];
+      unsigned long long cb = base + S.clo[b];
+      if (lo == hi) {
+        // one distinct value: its enclosed count is cb, and the bin test above
+        // was the exact predicate at that value
+        return (long long)lo;
+      }
+      if (S.cnt[b] <= (unsigned)cap) {
+        if (tid == 0) S.nlist = 0;
+        __syncthreads();
+        for (int j = tid; j < n; j += blockDim.x) {
+          unsigned long long d = (unsigned long long)ed[j];
+          if (d >= lo && d <= hi) S.list[atomicAdd(&S.nlist, 1)] = (long long)d;
+        }
+        __syncthreads();
+        int m = S.nlist;
+        int p2 = pow2_at_least(m);
+        for (int j = m + tid; j < p2; j += blockDim.x) S.list[j] = LLONG_MAX;
+        __syncthreads();
+        bitonic_sort(S.list, p2);
+        int k = scan_sorted(S.list, m, cb, c, &S.best);
+        if (k < m) {
+          long long r = S.list[k];
+          __syncthreads();
+          return r;
+        }
+        from = b + 1;
+        continue;
+      }
+      // too many members in the bin: narrow the window to it
+      wlo = lo;
+      whi = hi;
+      base = cb;
+      mode = 1;
+      narrowed = true;
+      break;
+    }
+    if (narrowed) continue;
+    // nothing in [wlo, whi]: move past it
+    base += in_window;
+    if (whi >= S.dmax_all) break;
+    wlo = whi + 1;
+    whi = S.dmax_all;
+    mode = 1;
+  }
+  long long r = 0;
+  if (tid == 0) S.list[0] = exhaust_radius((unsigned long long)n, (long long)S.dmax_all, c);
+  __syncthreads();
+  r = S.list[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
+  __shared__ SelShared S;
+  __shared__ int sP, sNc;
+  const int seg = blockIdx.x;
+  const unsigned base = a.seg_off[seg];
+  const int n = (int)(a.seg_off[seg + 1] - base);
+  const int tid = threadIdx.x;
+  const int4* epos = a.epos + base;
+  const long long* esig = a.esig + base;
+  int* eslot = a.eslot + base;
+  long long* edold = a.edold + base;
+  uint8_t* einel = a.einel + base;
+  long long* ed = a.ed + base;
+  uint32_t* ecand = a.ecand + base;
+
+  for (int j = tid; j < n; j += blockDim.x) {
+    eslot[j] = -1;
+    einel[j] = 0;
+  }
+  // step 4: candidates are the members above the stop level: a prefix in key order
+  if (tid == 0) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (esig[mid] > a.T_min) lo = mid + 1;
+      else hi = mid;
+    }
+    sP = lo;
+    sNc = 0;
+  }
+  __syncthreads();
+  const int P = sP;
+  // ordered list of local peaks among them (step 2's density criterion)
+  for (int c0 = 0; c0 < P; c0 += blockDim.x) {
+    int j = c0 + tid;
+    unsigned f = (j < P && a.epeak[base + j]) ? 1u : 0u;
+    unsigned excl;
+    unsigned tot = block_scan(f, excl, S.sw);
+    if (f) ecand[sNc + excl] = (uint32_t)j;
+    __syncthreads();
+    if (tid == 0) sNc += tot;
+    __syncthreads();
+  }
+  const int ncand = sNc;
+  const long long anum2 = (long long)a.alpha_num * a.alpha_num, aden2 = (long long)a.alpha_den * a.alpha_den;
+  int nn = 0;
+  for (int k = 0; k < ncand; ++k) {
+    const int cidx = (int)ecand[k];
+    if (einel[cidx]) continue;  // step 2: only eligible particles seed nuclei
+    const int4 pc = epos[cidx];
+    const long long R2 = r_search(epos, ed, n, pc, a.pc, S, a.small_n, a.cap, a.nb);
+    // steps 1 and 3
+    for (int j = tid; j < n; j += blockDim.x) {
+      long long d = ed[j];
+      if (d >= R2) continue;
+      int s = eslot[j];
+      bool take;
+      if (s < 0) {
+        take = true;
+      } else {
+        long long R2old = a.nuc_R2[base + s];
+        __int128 lhs = (__int128)R2 * edold[j] * a.roche_den;
+        __int128 rhs = (__int128)a.roche_num * R2old * d;
+        take = lhs >= rhs;
+      }
+      if (take) {
+        eslot[j] = nn;
+        edold[j] = d;
+      }
+      if ((__int128)aden2 * d < (__int128)anum2 * R2) einel[j] = 1;
+    }
+    if (tid == 0) {
+      a.nuc_member[base + nn] = (uint32_t)cidx;
+      a.nuc_R2[base + nn] = R2;
+    }
+    ++nn;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    a.nnuc[seg] = (uint32_t)nn;
+    if (a.work && nn) atomicAdd(a.work, (unsigned long long)nn * (unsigned long long)n);
+  }
+}
+
+// global halo index of every member (or -1) and per-halo nucleus records
+__global__ void k_level_halo(const uint32_t* __restrict__ seg_off, const uint32_t* __restrict__ nnuc,
+                             const uint32_t* __restrict__ hbase, const int* __restrict__ eslot,
+                             const uint32_t* __restrict__ nuc_member, const long long* __restrict__ nuc_R2,
+                             int* __restrict__ ehalo, uint32_t* __restrict__ hnuc, long long* __restrict__ hR2,
+                             uint32_t* __restrict__ hseg) {
+  const int seg = blockIdx.x;
+  const unsigned base = seg_off[seg];
+  const int n = (int)(seg_off[seg + 1] - base);
+  const unsigned hb = hbase[seg];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int s = eslot[base + j];
+    ehalo[base + j] = s < 0 ? -1 : (int)(hb + s);
+  }
+  for (int q = threadIdx.x; q < (int)nnuc[seg]; q += blockDim.x) {
+    hnuc[hb + q] = base + nuc_member[base + q];
+    hR2[hb + q] = nuc_R2[base + q];
+    hseg[hb + q] = seg;
+  }
+}
+
+}  // namespace
+
+int level_run(const LevelArgs& a, cudaStream_t st) {
+  if (a.nseg <= 0) return CSO_OK;
+  k_level<<<a.nseg, LV_THREADS, 0, st>>>(a);
+  CSO_CUDA(cudaGetLastError());
+  return CSO_OK;
+}
+
+int level_halo(int nseg, const uint32_t* seg_off, const uint32_t* nnuc, const uint32_t* hbase, const int* eslot,
+               const uint32_t* nuc_member, const long long* nuc_R2, int* ehalo, uint32_t* hnuc, long long* hR2,
+               uint32_t* hseg, cudaStream_t st) {
+  if (nseg <= 0) return CSO_OK;
+  k_level_halo<<<nseg, 256, 0, st>>>(seg_off, nnuc, hbase, eslot, nuc_member, nuc_R2, ehalo, hnuc, hR2, hseg);
+  CSO_CUDA(cudaGetLastError());
+  return CSO_OK;
+}
+
+PredConst make_pred_const(double K, long long u) {
+  PredConst c;
+  c.K = K;
+  int E;
+  double f = frexp(K, &E);
+  c.Km = (unsigned long long)ldexp(f, 53);
+  c.Ke = E - 53;
+  c.u = (unsigned long long)u;
+  double ud = (double)u;
+  c.u6 = ud * ud * ud * ud * ud * ud;
+  // bin of the first window: threshold count sqrt(K) d^1.5 / u^3 (before /w)
+  c.bin_scale0 = (float)(sqrt(K) / (ud * ud * ud));
+  return c;
+}

@@ -1,0 +1,42 @@
+// CompaSO level kernels (compaso.cu).
+#pragma once
+#include "cso_internal.cuh"
+
+// constants of the exact predicate n^2 u^6 < K d^3
+struct PredConst {
+  double K;                 // (Delta 4 pi / 3)^2
+  double u6;                // u^6 (double)
+  unsigned long long Km;    // K = Km * 2^Ke exactly
+  int Ke;
+  unsigned long long u;
+  float bin_scale0;         // sqrt(K) / u^3
+};
+PredConst make_pred_const(double K, long long u);
+
+struct LevelArgs {
+  int nseg;
+  const uint32_t* seg_off;  // nseg + 1 offsets into the element arrays
+  const int4* epos;         // member positions, key order within a segment
+  const long long* esig;    // kernel sums (descending within a segment)
+  const uint8_t* epeak;     // local-peak flags
+  long long T_min;
+  PredConst pc;
+  int alpha_num, alpha_den, roche_num, roche_den;
+  int* eslot;               // out: nucleus ordinal within the segment, or -1
+  long long* edold;         // scratch: squared distance to the current nucleus
+  uint8_t* einel;           // scratch: ineligible flags
+  long long* ed;            // scratch: distances to the nucleus being processed
+  uint32_t* ecand;          // scratch: candidate list
+  uint32_t* nuc_member;     // out: [seg_off + q] member offset of nucleus q
+  long long* nuc_R2;        // out: [seg_off + q] its squared radius
+  uint32_t* nnuc;           // out: nuclei per segment
+  unsigned long long* work; // optional: sum over nuclei of the segment size
+  int small_n;              // groups up to this size are sorted whole (<= 2048)
+  int cap;                  // largest histogram bin sorted in shared memory (<= 2048)
+  int nb;                   // histogram bins (<= 1024)
+};
+
+int level_run(const LevelArgs& a, cudaStream_t st);
+int level_halo(int nseg, const uint32_t* seg_off, const uint32_t* nnuc, const uint32_t* hbase, const int* eslot,
+               const uint32_t* nuc_member, const long long* nuc_R2, int* ehalo, uint32_t* hnuc, long long* hR2,
+               uint32_t* hseg, cudaStream_t st);

@@ -1,0 +1,640 @@
+// The plain pipeline: one box, all stages on the context's stream.
+//
+//   bin      counting sort of particles into the dense cell table
+//   density  Sigma per particle (Eq. 1)
+//   fof      L0 groups over dense particles (Sec. 2.2.1)
+//   gather   dense particles sorted by (L0 group, Sigma desc, id asc)
+//   peak1    local-peak flags within L0 groups (step 2)
+//   level1   CompaSO L1, block per L0 group (steps 1-4)
+//   prep2    members of each L1 halo in key order, peak flags within L1
+//   level2   CompaSO L2, block per L1 halo
+//   output   labels in input order, per-halo statistics, catalogue
+#include <string.h>
+
+#include "cells.cuh"
+#include "compaso.cuh"
+#include "pipeline.cuh"
+
+namespace {
+
+constexpr unsigned long long NONE = ~0ull;
+
+struct Meta {  // device counters read back by the host
+  unsigned long long sigma_max, id_max;
+  unsigned long long pairs, work1, work2;
+  int bad;
+  unsigned pad;
+};
+
+__global__ void k_flags(const int* __restrict__ root, int n, uint32_t* __restrict__ dflag,
+                        uint32_t* __restrict__ rflag) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int r = root[s];
+  dflag[s] = r >= 0;
+  rflag[s] = r == s;
+}
+
+__global__ void k_compact_dense(const int* __restrict__ root, int n, const uint32_t* __restrict__ dscan,
+                                const long long* __restrict__ sigma, const uint64_t* __restrict__ sid,
+                                uint32_t* __restrict__ dl, Meta* meta) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || root[s] < 0) return;
+  dl[dscan[s]] = (uint32_t)s;
+  atomicMax(&meta->sigma_max, (unsigned long long)sigma[s]);
+  atomicMax(&meta->id_max, (unsigned long long)sid[s]);
+}
+
+// key = group | (Sigma_max - Sigma) | id, packed low to high: id, Sigma', group
+__global__ void k_make_keys(const uint32_t* __restrict__ dl, int nd, const int* __restrict__ root,
+                            const uint32_t* __restrict__ rscan, const long long* __restrict__ sigma,
+                            const uint64_t* __restrict__ sid, unsigned long long sigma_max, int bits_id,
+                            int bits_sig, uint64_t* __restrict__ khi, uint64_t* __restrict__ klo,
+                            uint32_t* __restrict__ val) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nd) return;
+  uint32_t s = dl[k];
+  unsigned __int128 g = rscan[root[s]];
+  unsigned __int128 sp = sigma_max - (unsigned long long)sigma[s];
+  unsigned __int128 key = (g << (bits_sig + bits_id)) | (sp << bits_id) | (unsigned __int128)sid[s];
+  khi[k] = (uint64_t)(key >> 64);
+  klo[k] = (uint64_t)key;
+  val[k] = s;
+}
+
+__global__ void k_seg_bounds128(const uint64_t* __restrict__ khi, const uint64_t* __restrict__ klo, int nd,
+                                int gshift, int nseg, uint32_t* __restrict__ seg_off) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nd) return;
+  auto grp = [&](int i) -> unsigned long long {
+    unsigned __int128 key = ((unsigned __int128)(khi ? khi[i] : 0) << 64) | klo[i];
+    return (unsigned long long)(key >> gshift);
+  };
+  unsigned long long g = grp(k);
+  if (k == 0 || grp(k - 1) != g) seg_off[g] = k;
+  if (k == nd - 1) seg_off[nseg] = nd;
+}
+
+__global__ void k_seg_bounds32(const uint32_t* __restrict__ key, int m, int nseg, uint32_t* __restrict__ seg_off) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  uint32_t g = key[k];
+  if (k == 0 || key[k - 1] != g) seg_off[g] = k;
+  if (k == m - 1) seg_off[nseg] = m;
+}
+
+__global__ void k_gather1(const uint32_t* __restrict__ val, int nd, const int4* __restrict__ spos,
+                          const long long* __restrict__ sigma, const uint64_t* __restrict__ sid,
+                          int4* __restrict__ epos, long long* __restrict__ esig, uint64_t* __restrict__ eid) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nd) return;
+  uint32_t s = val[k];
+  epos[k] = spos[s];
+  esig[k] = sigma[s];
+  eid[k] = sid[s];
+}
+
+__global__ void k_gather_u8(const uint32_t* __restrict__ idx, int m, const uint8_t* __restrict__ src,
+                            uint8_t* __restrict__ dst) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < m) dst[k] = src[idx[k]];
+}
+
+__global__ void k_flag_assigned(const int* __restrict__ ehalo, int nd, uint32_t* __restrict__ f) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nd) f[k] = ehalo[k] >= 0;
+}
+
+__global__ void k_compact_assigned(const int* __restrict__ ehalo, int nd, const uint32_t* __restrict__ scan,
+                                   const uint32_t* __restrict__ gs, uint32_t* __restrict__ key,
+                                   uint32_t* __restrict__ val, int* __restrict__ lab1) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nd) return;
+  int h = ehalo[k];
+  if (h < 0) return;
+  key[scan[k]] = (uint32_t)h;
+  val[scan[k]] = (uint32_t)k;
+  lab1[gs[k]] = h;
+}
+
+__global__ void k_gather2(const uint32_t* __restrict__ ek, int m, const int4* __restrict__ epos,
+                          const long long* __restrict__ esig, const uint32_t* __restrict__ gs,
+                          const uint8_t* __restrict__ peak2, int4* __restrict__ epos2, long long* __restrict__ esig2,
+                          uint8_t* __restrict__ epeak2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  uint32_t k = ek[i];
+  epos2[i] = epos[k];
+  esig2[i] = esig[k];
+  epeak2[i] = peak2[gs[k]];
+}
+
+__global__ void k_fill_u64(uint64_t* p, long long n, uint64_t v) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void k_out_cells(const int4* __restrict__ spos, int n, const long long* __restrict__ sigma,
+                            const int* __restrict__ root, const unsigned long long* __restrict__ minid,
+                            int64_t* __restrict__ osig, uint64_t* __restrict__ ol0) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int orig = spos[s].w;
+  if (osig) osig[orig] = sigma[s];
+  if (ol0) {
+    int r = root[s];
+    ol0[orig] = r >= 0 ? minid[r] : NONE;
+  }
+}
+
+__global__ void k_out_l1(const int* __restrict__ ehalo, int nd, const uint32_t* __restrict__ gs,
+                         const int4* __restrict__ spos, const uint32_t* __restrict__ hnuc,
+                         const uint64_t* __restrict__ eid, uint64_t* __restrict__ ol1) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nd) return;
+  int h = ehalo[k];
+  if (h >= 0) ol1[spos[gs[k]].w] = eid[hnuc[h]];
+}
+
+__global__ void k_out_l2(const int* __restrict__ ehalo2, int m, const uint32_t* __restrict__ ek2,
+                         const uint32_t* __restrict__ gs, const int4* __restrict__ spos,
+                         const uint32_t* __restrict__ hnuc2, const uint64_t* __restrict__ eid,
+                         uint64_t* __restrict__ ol2, unsigned* __restrict__ h2size) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int h = ehalo2[i];
+  if (h < 0) return;
+  atomicAdd(&h2size[h], 1u);
+  if (ol2) ol2[spos[gs[ek2[i]]].w] = eid[ek2[hnuc2[h]]];
+}
+
+__device__ __forceinline__ int mi(int v) {
+  if (v >= CSO_HALF) return v - CSO_BOX;
+  if (v < -CSO_HALF) return v + CSO_BOX;
+  return v;
+}
+
+__device__ __forceinline__ double wrap_box(double c) {
+  if (c < 0) c += (double)CSO_BOX;
+  if (c >= (double)CSO_BOX) c -= (double)CSO_BOX;
+  return c;
+}
+
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* sh) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+  __syncthreads();
+  return t;
+}
+
+// one block per L1 halo: statistics over its members (the L2-level segment)
+__global__ void __launch_bounds__(256) k_summary(
+    const uint32_t* __restrict__ seg2, const int4* __restrict__ epos2, const int* __restrict__ ehalo2,
+    const uint32_t* __restrict__ ek2, const uint32_t* __restrict__ hnuc, const long long* __restrict__ hR2,
+    const int4* __restrict__ epos, const uint64_t* __restrict__ eid, const uint32_t* __restrict__ gs,
+    const int* __restrict__ root, const unsigned long long* __restrict__ minid, const uint32_t* __restrict__ nnuc2,
+    const uint32_t* __restrict__ hbase2, const uint32_t* __restrict__ hnuc2, const unsigned* __restrict__ h2size,
+    double inv_u, int np_min, cso_halo* __restrict__ rows, uint32_t* __restrict__ keep) {
+  __shared__ long long sh[8];
+  const int h = blockIdx.x;
+  const unsigned b = seg2[h];
+  const int n = (int)(seg2[h + 1] - b);
+  const uint32_t kn = hnuc[h];
+  const int4 pn = epos[kn];
+  const int nl2 = (int)nnuc2[h];
+  const int first2 = (int)hbase2[h];
+  int4 p2 = pn;
+  if (nl2 > 0) p2 = epos2[hnuc2[first2]];
+  long long sx = 0, sy = 0, sz = 0, tx = 0, ty = 0, tz = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int4 q = epos2[b + i];
+    sx += mi(q.x - pn.x);
+    sy += mi(q.y - pn.y);
+    sz += mi(q.z - pn.z);
+    if (nl2 > 0 && ehalo2[b + i] == first2) {
+      tx += mi(q.x - p2.x);
+      ty += mi(q.y - p2.y);
+      tz += mi(q.z - p2.z);
+    }
+  }
+  sx = block_sum_ll(sx, sh);
+  sy = block_sum_ll(sy, sh);
+  sz = block_sum_ll(sz, sh);
+  tx = block_sum_ll(tx, sh);
+  ty = block_sum_ll(ty, sh);
+  tz = block_sum_ll(tz, sh);
+  if (threadIdx.x != 0) return;
+  cso_halo r;
+  r.nucleus_id = eid[kn];
+  r.N = n;
+  r.R2 = hR2[h];
+  r.R_delta = sqrt((double)r.R2) * inv_u;
+  r.com[0] = wrap_box((double)pn.x + (double)sx / (double)n);
+  r.com[1] = wrap_box((double)pn.y + (double)sy / (double)n);
+  r.com[2] = wrap_box((double)pn.z + (double)sz / (double)n);
+  r.l0_id = minid[root[gs[kn]]];
+  r.n_l2 = nl2;
+  for (int k = 0; k < 5; ++k) r.l2_top5_N[k] = 0;
+  if (nl2 > 0) {
+    long long n2 = h2size[first2];
+    r.l2max_id = eid[ek2[hnuc2[first2]]];
+    r.l2max_N = n2;
+    r.l2max_com[0] = wrap_box((double)p2.x + (double)tx / (double)n2);
+    r.l2max_com[1] = wrap_box((double)p2.y + (double)ty / (double)n2);
+    r.l2max_com[2] = wrap_box((double)p2.z + (double)tz / (double)n2);
+    for (int q = 0; q < nl2; ++q) {  // five largest sizes, descending
+      long long v = h2size[first2 + q];
+      for (int k = 0; k < 5; ++k)
+        if (v > r.l2_top5_N[k]) {
+          long long t = r.l2_top5_N[k];
+          r.l2_top5_N[k] = v;
+          v = t;
+        }
+    }
+  } else {
+    r.l2max_id = NONE;
+    r.l2max_N = 0;
+    r.l2max_com[0] = r.l2max_com[1] = r.l2max_com[2] = 0.0;
+  }
+  rows[h] = r;
+  keep[h] = n >= np_min;
+}
+
+__global__ void k_catalogue_keys(const cso_halo* __restrict__ rows, const uint32_t* __restrict__ keep,
+                                 const uint32_t* __restrict__ kscan, int H, uint64_t* __restrict__ key,
+                                 uint32_t* __restrict__ val) {
+  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H || !keep[h]) return;
+  key[kscan[h]] = rows[h].nucleus_id;
+  val[kscan[h]] = (uint32_t)h;
+}
+
+__global__ void k_catalogue_write(const cso_halo* __restrict__ rows, const uint32_t* __restrict__ order, int m,
+                                  cso_halo* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) out[i] = rows[order[i]];
+}
+
+struct Stages {
+  cso_ctx* c;
+  bool on;
+  int k = 0;
+  void mark(const char* name) {
+    if (!on || k >= CSO_MAX_STAGES) return;
+    cudaEventRecord(c->ev[k], c->stream);
+    c->stage_name[k] = name;
+    ++k;
+  }
+  void finish() {
+    if (!on) return;
+    cudaEventRecord(c->ev[k], c->stream);
+    cudaEventSynchronize(c->ev[k]);
+    for (int i = 0; i < k; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+      c->stage_ms[i] = ms;
+    }
+    c->nstages = k;
+  }
+};
+
+int readback(cso_ctx* c, const void* dev, size_t bytes) {
+  CSO_CUDA(cudaMemcpyAsync(c->pinned, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+  CSO_CUDA(cudaStreamSynchronize(c->stream));
+  return CSO_OK;
+}
+
+#define G1(n) cdiv((n), 256), 256, 0, st
+
+}  // namespace
+
+int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out) {
+  cudaStream_t st = c->stream;
+  const long long n = in->n;
+  memset(c->stats, 0, sizeof(c->stats));
+  c->stats[0] = n;
+  c->nstages = 0;
+  out->n_halos = 0;
+  if (n == 0) return CSO_OK;
+  int nc;
+  CSO_TRY(cells_choose(p->b2, &nc));
+  const long long ncell = (long long)nc * nc * nc;
+  const bool host_in = !in->on_device, host_out = !out->on_device;
+  CSO_TRY(ctx_reserve(c, n, ncell, host_in || host_out));
+  Workspace& ws = c->ws;
+  Stages S{c, (c->flags & CSO_FLAG_TIMING) != 0};
+  const int N = (int)n;
+
+#define ALLOC(T, name, cnt)                              \
+  T* name = ws.get<T>(cnt);                              \
+  if (!name) {                                           \
+    cso_set_error("workspace exhausted (%s)", #name);    \
+    return CSO_ERR_BUDGET;                               \
+  }
+
+  // ---- inputs ----
+  S.mark("h2d");
+  const int32_t* pos = in->pos;
+  const uint64_t* ids = in->ids;
+  if (host_in) {
+    ALLOC(int32_t, dpos, 3 * n);
+    ALLOC(uint64_t, dids, n);
+    CSO_CUDA(cudaMemcpyAsync(dpos, in->pos, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, st));
+    CSO_CUDA(cudaMemcpyAsync(dids, in->ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
+    pos = dpos;
+    ids = dids;
+  }
+  ALLOC(Meta, meta, 1);
+  CSO_CUDA(cudaMemsetAsync(meta, 0, sizeof(Meta), st));
+
+  // ---- bin ----
+  S.mark("bin");
+  ALLOC(uint32_t, start, ncell + 1);
+  ALLOC(int4, spos, n);
+  ALLOC(uint64_t, sid, n);
+  CSO_TRY(cells_bin(pos, ids, n, nc, start, spos, sid, &meta->bad, ws, st));
+  CellGrid g{nc, start};
+
+  // ---- density ----
+  S.mark("density");
+  ALLOC(long long, sigma, n);
+  const bool count_pairs = (c->flags & CSO_FLAG_COUNT_PAIRS) != 0;
+  CSO_TRY(cells_density(g, spos, N, (uint32_t)p->b2, p->include_self, sigma, count_pairs ? &meta->pairs : nullptr,
+                        st));
+
+  // ---- fof ----
+  S.mark("fof");
+  ALLOC(int, parent, n);
+  ALLOC(int, root, n);
+  ALLOC(unsigned long long, minid, n);
+  CSO_TRY(cells_fof(g, spos, N, sigma, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, st));
+
+  // ---- gather: dense particles by (group, Sigma desc, id asc) ----
+  S.mark("gather");
+  ALLOC(uint32_t, dscan, n + 1);
+  ALLOC(uint32_t, rscan, n + 1);
+  k_flags<<<G1(n)>>>(root, N, dscan, rscan);
+  CSO_TRY(scan_u32(dscan, n, dscan + n, ws, st));
+  CSO_TRY(scan_u32(rscan, n, rscan + n, ws, st));
+  ALLOC(uint32_t, dl, n);
+  k_compact_dense<<<G1(n)>>>(root, N, dscan, sigma, sid, dl, meta);
+  CSO_CUDA(cudaGetLastError());
+  // counters: n_dense, G, sigma_max, id_max, bad
+  {
+    CSO_CUDA(cudaMemcpyAsync(c->pinned, dscan + n, 4, cudaMemcpyDeviceToHost, st));
+    CSO_CUDA(cudaMemcpyAsync((char*)c->pinned + 4, rscan + n, 4, cudaMemcpyDeviceToHost, st));
+    CSO_CUDA(cudaMemcpyAsync(c->pinned + 1, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
+    CSO_CUDA(cudaStreamSynchronize(st));
+  }
+  const int nd = (int)((uint32_t*)c->pinned)[0];
+  const int G = (int)((uint32_t*)c->pinned)[1];
+  Meta hm;
+  memcpy(&hm, c->pinned + 1, sizeof(Meta));
+  if (hm.bad) {
+    cso_set_error("positions outside [0, 2^21)");
+    return CSO_ERR_ARG;
+  }
+  c->stats[1] = nd;
+  c->stats[2] = G;
+  if (count_pairs) c->stats[6] = (int64_t)hm.pairs;
+
+  const int bits_id = bit_length_u64(hm.id_max);
+  const int bits_sig = nd ? bit_length_u64(hm.sigma_max - (unsigned long long)(p->T_L0 + 1)) : 0;
+  const int bits_g = bit_length_u64(G > 0 ? (unsigned long long)(G - 1) : 0);
+  if (bits_id + bits_sig + bits_g > 128) {
+    cso_set_error("sort key of %d bits exceeds 128", bits_id + bits_sig + bits_g);
+    return CSO_ERR_ARG;
+  }
+  ALLOC(uint64_t, khi, nd);
+  ALLOC(uint64_t, klo, nd);
+  ALLOC(uint32_t, kval, nd);
+  ALLOC(uint64_t, khi2, nd);
+  ALLOC(uint64_t, klo2, nd);
+  ALLOC(uint32_t, kval2, nd);
+  ALLOC(uint32_t, seg1, G + 1);
+  ALLOC(int4, epos, nd);
+  ALLOC(long long, esig, nd);
+  ALLOC(uint64_t, eid, nd);
+  ALLOC(uint8_t, epeak, nd);
+  uint32_t* gs = kval;
+  if (nd > 0) {
+    k_make_keys<<<G1(nd)>>>(dl, nd, root, rscan, sigma, sid, hm.sigma_max, bits_id, bits_sig, khi, klo, kval);
+    uint64_t *ph = khi, *pl = klo;
+    uint32_t* pv = kval;
+    int bits = bits_id + bits_sig + bits_g;
+    CSO_TRY(radix_sort_128(&ph, &pl, &pv, khi2, klo2, kval2, nd, bits, ws, st));
+    k_seg_bounds128<<<G1(nd)>>>(bits > 64 ? ph : nullptr, pl, nd, bits_sig + bits_id, G, seg1);
+    gs = pv;
+    k_gather1<<<G1(nd)>>>(gs, nd, spos, sigma, sid, epos, esig, eid);
+    CSO_CUDA(cudaGetLastError());
+  }
+
+  // ---- peak1 ----
+  S.mark("peak1");
+  ALLOC(uint8_t, peak, n);
+  CSO_TRY(cells_peak(g, spos, N, sigma, sid, root, p->T_min_L1, (uint32_t)p->b2, peak, st));
+  if (nd > 0) k_gather_u8<<<G1(nd)>>>(gs, nd, peak, epeak);
+
+  // ---- level1 ----
+  S.mark("level1");
+  ALLOC(int, eslot, nd);
+  ALLOC(long long, edold, nd);
+  ALLOC(uint8_t, einel, nd);
+  ALLOC(long long, ed, nd);
+  ALLOC(uint32_t, ecand, nd);
+  ALLOC(uint32_t, nucm, nd);
+  ALLOC(long long, nucR2, nd);
+  ALLOC(uint32_t, nnuc, G + 1);
+  LevelArgs L1{};
+  L1.nseg = G;
+  L1.seg_off = seg1;
+  L1.epos = epos;
+  L1.esig = esig;
+  L1.epeak = epeak;
+  L1.T_min = p->T_min_L1;
+  L1.pc = make_pred_const(p->K_L1, (long long)p->l_mean_grid);
+  L1.alpha_num = p->alpha_num;
+  L1.alpha_den = p->alpha_den;
+  L1.roche_num = p->roche_num;
+  L1.roche_den = p->roche_den;
+  L1.eslot = eslot;
+  L1.edold = edold;
+  L1.einel = einel;
+  L1.ed = ed;
+  L1.ecand = ecand;
+  L1.nuc_member = nucm;
+  L1.nuc_R2 = nucR2;
+  L1.nnuc = nnuc;
+  L1.work = &meta->work1;
+  const bool stress = (c->flags & CSO_FLAG_SELECT_STRESS) != 0;
+  L1.small_n = stress ? 8 : 2048;
+  L1.cap = stress ? 8 : 2048;
+  L1.nb = stress ? 16 : 1024;
+  CSO_TRY(level_run(L1, st));
+
+  // ---- prep2: L1 haloes, their members in key order, peaks within L1 ----
+  S.mark("prep2");
+  ALLOC(uint32_t, hbase, G + 1);
+  if (G > 0) CSO_CUDA(cudaMemcpyAsync(hbase, nnuc, sizeof(uint32_t) * G, cudaMemcpyDeviceToDevice, st));
+  CSO_TRY(scan_u32(hbase, G, hbase + G, ws, st));
+  ALLOC(uint32_t, aflag, nd + 1);
+  ALLOC(int, ehalo, nd);
+  if (nd > 0) k_flag_assigned<<<G1(nd)>>>(eslot, nd, aflag);  // slot >= 0 <=> assigned
+  CSO_TRY(scan_u32(aflag, nd, aflag + nd, ws, st));
+  CSO_CUDA(cudaMemcpyAsync(c->pinned, hbase + G, 4, cudaMemcpyDeviceToHost, st));
+  CSO_CUDA(cudaMemcpyAsync((char*)c->pinned + 4, aflag + nd, 4, cudaMemcpyDeviceToHost, st));
+  CSO_CUDA(cudaStreamSynchronize(st));
+  const int H1 = (int)((uint32_t*)c->pinned)[0];
+  const int na = (int)((uint32_t*)c->pinned)[1];
+  c->stats[3] = H1;
+  ALLOC(uint32_t, hnuc, H1);
+  ALLOC(long long, hR2, H1);
+  ALLOC(uint32_t, hseg, H1);
+  CSO_TRY(level_halo(G, seg1, nnuc, hbase, eslot, nucm, nucR2, ehalo, hnuc, hR2, hseg, st));
+  ALLOC(int, lab1, n);
+  CSO_CUDA(cudaMemsetAsync(lab1, 0xff, sizeof(int) * n, st));
+  ALLOC(uint32_t, akey, na);
+  ALLOC(uint32_t, aval, na);
+  ALLOC(uint32_t, akey2, na);
+  ALLOC(uint32_t, aval2, na);
+  ALLOC(uint32_t, seg2, H1 + 1);
+  uint32_t* ek2 = aval;
+  if (nd > 0) k_compact_assigned<<<G1(nd)>>>(ehalo, nd, aflag, gs, akey, aval, lab1);
+  if (na > 0) {
+    uint32_t *pk = akey, *pv = aval;
+    CSO_TRY(radix_sort_32(&pk, &pv, akey2, aval2, na, bit_length_u64(H1 > 0 ? H1 - 1 : 0), ws, st));
+    k_seg_bounds32<<<G1(na)>>>(pk, na, H1, seg2);
+    ek2 = pv;
+  }
+  ALLOC(uint8_t, peak2, n);
+  CSO_TRY(cells_peak(g, spos, N, sigma, sid, lab1, p->T_min_L2, (uint32_t)p->b2, peak2, st));
+  ALLOC(int4, epos2, na);
+  ALLOC(long long, esig2, na);
+  ALLOC(uint8_t, epeak2, na);
+  if (na > 0) k_gather2<<<G1(na)>>>(ek2, na, epos, esig, gs, peak2, epos2, esig2, epeak2);
+  CSO_CUDA(cudaGetLastError());
+
+  // ---- level2 ----
+  S.mark("level2");
+  ALLOC(int, eslot2, na);
+  ALLOC(uint32_t, nucm2, na);
+  ALLOC(long long, nucR22, na);
+  ALLOC(uint32_t, nnuc2, H1 + 1);
+  LevelArgs L2 = L1;
+  L2.nseg = H1;
+  L2.seg_off = seg2;
+  L2.epos = epos2;
+  L2.esig = esig2;
+  L2.epeak = epeak2;
+  L2.T_min = p->T_min_L2;
+  L2.pc = make_pred_const(p->K_L2, (long long)p->l_mean_grid);
+  L2.eslot = eslot2;
+  L2.nuc_member = nucm2;
+  L2.nuc_R2 = nucR22;
+  L2.nnuc = nnuc2;
+  L2.work = &meta->work2;
+  CSO_TRY(level_run(L2, st));  // edold / einel / ed / ecand are reused (na <= nd)
+
+  // ---- output ----
+  S.mark("output");
+  ALLOC(uint32_t, hbase2, H1 + 1);
+  if (H1 > 0) CSO_CUDA(cudaMemcpyAsync(hbase2, nnuc2, sizeof(uint32_t) * H1, cudaMemcpyDeviceToDevice, st));
+  CSO_TRY(scan_u32(hbase2, H1, hbase2 + H1, ws, st));
+  CSO_TRY(readback(c, hbase2 + H1, 4));
+  const int H2 = (int)((uint32_t*)c->pinned)[0];
+  c->stats[4] = H2;
+  ALLOC(int, ehalo2, na);
+  ALLOC(uint32_t, hnuc2, H2);
+  ALLOC(long long, hR2b, H2);
+  ALLOC(uint32_t, hseg2, H2);
+  ALLOC(unsigned, h2size, H2);
+  CSO_TRY(level_halo(H1, seg2, nnuc2, hbase2, eslot2, nucm2, nucR22, ehalo2, hnuc2, hR2b, hseg2, st));
+  if (H2 > 0) CSO_CUDA(cudaMemsetAsync(h2size, 0, sizeof(unsigned) * H2, st));
+
+  uint64_t *ol0 = out->l0, *ol1 = out->l1, *ol2 = out->l2;
+  int64_t* osig = out->sigma;
+  if (host_out) {
+    if (ol0) { ALLOC(uint64_t, t, n); ol0 = t; }
+    if (ol1) { ALLOC(uint64_t, t, n); ol1 = t; }
+    if (ol2) { ALLOC(uint64_t, t, n); ol2 = t; }
+    if (osig) { ALLOC(int64_t, t, n); osig = t; }
+  }
+  if (ol1) k_fill_u64<<<G1(n)>>>(ol1, n, NONE);
+  if (ol2) k_fill_u64<<<G1(n)>>>(ol2, n, NONE);
+  k_out_cells<<<G1(n)>>>(spos, N, sigma, root, minid, osig, ol0);
+  if (ol1 && nd > 0) k_out_l1<<<G1(nd)>>>(ehalo, nd, gs, spos, hnuc, eid, ol1);
+  if (na > 0) k_out_l2<<<G1(na)>>>(ehalo2, na, ek2, gs, spos, hnuc2, eid, ol2, h2size);
+  CSO_CUDA(cudaGetLastError());
+
+  // per-halo rows and the catalogue
+  if ((size_t)H1 * 2 > c->rows_cap) {
+    if (c->rows) {
+      CSO_CUDA(cudaStreamSynchronize(st));
+      CSO_CUDA(cudaFree(c->rows));
+      c->rows = nullptr;
+    }
+    size_t cap = (size_t)H1 * 2 + 1024;
+    CSO_CUDA(cudaMalloc((void**)&c->rows, sizeof(cso_halo) * cap));
+    c->rows_cap = cap;
+  }
+  cso_halo* rows = c->rows;
+  cso_halo* sorted_rows = c->rows + H1;
+  ALLOC(uint32_t, keep, H1 + 1);
+  int nrows = 0;
+  if (H1 > 0) {
+    k_summary<<<H1, 256, 0, st>>>(seg2, epos2, ehalo2, ek2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2,
+                                   h2size, 1.0 / p->l_mean_grid, p->np_min_L1, rows, keep);
+    CSO_CUDA(cudaGetLastError());
+    ALLOC(uint32_t, kscan, H1 + 1);
+    CSO_CUDA(cudaMemcpyAsync(kscan, keep, sizeof(uint32_t) * H1, cudaMemcpyDeviceToDevice, st));
+    CSO_TRY(scan_u32(kscan, H1, kscan + H1, ws, st));
+    CSO_TRY(readback(c, kscan + H1, 4));
+    nrows = (int)((uint32_t*)c->pinned)[0];
+    ALLOC(uint64_t, ckey, nrows);
+    ALLOC(uint32_t, cval, nrows);
+    ALLOC(uint64_t, ckey2, nrows);
+    ALLOC(uint32_t, cval2, nrows);
+    if (nrows > 0) {
+      k_catalogue_keys<<<G1(H1)>>>(rows, keep, kscan, H1, ckey, cval);
+      uint64_t* ph = nullptr;
+      uint64_t* pl = ckey;
+      uint32_t* pv = cval;
+      CSO_TRY(radix_sort_128(&ph, &pl, &pv, nullptr, ckey2, cval2, nrows, bit_length_u64(hm.id_max), ws, st));
+      k_catalogue_write<<<G1(nrows)>>>(rows, pv, nrows, sorted_rows);
+      CSO_CUDA(cudaGetLastError());
+    }
+  }
+  out->n_halos = nrows;
+  c->stats[5] = nrows;
+  const int ncopy = nrows <= out->halo_cap ? nrows : 0;
+  if (ncopy > 0)
+    CSO_CUDA(cudaMemcpyAsync(out->halos, sorted_rows, sizeof(cso_halo) * ncopy,
+                             host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+
+  // ---- d2h ----
+  S.mark("d2h");
+  if (host_out) {
+    if (out->l0) CSO_CUDA(cudaMemcpyAsync(out->l0, ol0, 8 * n, cudaMemcpyDeviceToHost, st));
+    if (out->l1) CSO_CUDA(cudaMemcpyAsync(out->l1, ol1, 8 * n, cudaMemcpyDeviceToHost, st));
+    if (out->l2) CSO_CUDA(cudaMemcpyAsync(out->l2, ol2, 8 * n, cudaMemcpyDeviceToHost, st));
+    if (out->sigma) CSO_CUDA(cudaMemcpyAsync(out->sigma, osig, 8 * n, cudaMemcpyDeviceToHost, st));
+  }
+  S.finish();
+  CSO_CUDA(cudaMemcpyAsync(c->pinned, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
+  CSO_CUDA(cudaStreamSynchronize(st));
+  memcpy(&hm, c->pinned, sizeof(Meta));
+  c->stats[7] = (int64_t)hm.work1;
+  c->stats[8] = (int64_t)hm.work2;
+  c->stats[9] = (int64_t)ws.peak;
+#undef ALLOC
+  if (nrows > out->halo_cap) {
+    cso_set_error("catalogue has %d rows, halo_cap is %lld", nrows, (long long)out->halo_cap);
+    return CSO_ERR_CAPACITY;
+  }
+  return CSO_OK;
+}

@@ -1,0 +1,288 @@
+// Device-wide exclusive scan and stable LSD radix sort (8-bit digits).
+//
+// The radix sort ranks elements inside a tile with warp-level matching
+// (__match_any_sync): warp w owns a contiguous run of the tile and keeps a
+// running per-digit counter in shared memory, so ranks are stable; per-warp
+// counts are then prefixed across warps and offset by the tile's global
+// digit base from the scanned [digit][tile] histogram.
+#include "cso_internal.cuh"
+
+namespace {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the block total
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem_warp, uint32_t& excl) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) smem_warp[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = lane < nw ? smem_warp[lane] : 0;
+    uint32_t si = warp_incl_scan(s);
+    if (lane < nw) smem_warp[lane] = si - s;
+    if (lane == 31) smem_warp[32] = si;
+  }
+  __syncthreads();
+  excl = inc - v + smem_warp[w];
+  uint32_t total = smem_warp[32];
+  __syncthreads();
+  return total;
+}
+
+__global__ void k_tile_sums(const uint32_t* __restrict__ d, long long n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t sw[33];
+  long long base = (long long)blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    long long i = base + (long long)k * SCAN_THREADS + threadIdx.x;
+    if (i < n) s += d[i];
+  }
+  uint32_t excl;
+  uint32_t tot = block_excl_scan(s, sw, excl);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of m values (any m), total to *total
+__global__ void k_scan_single(uint32_t* __restrict__ d, long long m, uint32_t* total) {
+  __shared__ uint32_t sw[33];
+  uint32_t carry = 0;
+  for (long long base = 0; base < m; base += (long long)blockDim.x * SCAN_ITEMS) {
+    // each thread owns SCAN_ITEMS consecutive values
+    long long i0 = base + (long long)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      v[k] = (i0 + k < m) ? d[i0 + k] : 0;
+      s += v[k];
+    }
+    uint32_t excl;
+    uint32_t tot = block_excl_scan(s, sw, excl);
+    uint32_t run = carry + excl;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      if (i0 + k < m) d[i0 + k] = run;
+      run += v[k];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_tiles(uint32_t* __restrict__ d, long long n, const uint32_t* __restrict__ sums) {
+  __shared__ uint32_t sw[33];
+  long long base = (long long)blockIdx.x * SCAN_TILE;
+  long long i0 = base + (long long)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (i0 + k < n) ? d[i0 + k] : 0;
+    s += v[k];
+  }
+  uint32_t excl;
+  block_excl_scan(s, sw, excl);
+  uint32_t run = sums[blockIdx.x] + excl;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (i0 + k < n) d[i0 + k] = run;
+    run += v[k];
+  }
+}
+
+// --------------------------------------------------------------------------
+// radix sort
+// --------------------------------------------------------------------------
+constexpr int RS_WARPS = 8;
+constexpr int RS_THREADS = RS_WARPS * 32;
+constexpr int RS_ITEMS = 8;                       // per lane
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;    // 2048
+constexpr int RS_RADIX = 256;
+
+struct Key128 {
+  const uint64_t* hi;
+  const uint64_t* lo;
+  // shifts are multiples of 8, so a digit never straddles the two words
+  __device__ __forceinline__ uint32_t digit(long long i, int shift) const {
+    if (shift < 64) return (uint32_t)(lo[i] >> shift) & 0xffu;
+    return (uint32_t)(hi[i] >> (shift - 64)) & 0xffu;
+  }
+};
+
+struct Key32 {
+  const uint32_t* k;
+  __device__ __forceinline__ uint32_t digit(long long i, int shift) const { return (k[i] >> shift) & 0xffu; }
+};
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(K key, long long n, int shift, uint32_t* __restrict__ hist,
+                                                      int ntiles) {
+  __shared__ uint32_t h[RS_RADIX];
+  for (int t = threadIdx.x; t < RS_RADIX; t += RS_THREADS) h[t] = 0;
+  __syncthreads();
+  long long base = (long long)blockIdx.x * RS_TILE;
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    long long i = base + (long long)k * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[key.digit(i, shift)], 1u);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < RS_RADIX; t += RS_THREADS) hist[(long long)t * ntiles + blockIdx.x] = h[t];
+}
+
+template <class K, class MoveFn>
+__device__ __forceinline__ void rs_scatter_body(K key, long long n, int shift, const uint32_t* __restrict__ hist,
+                                                int ntiles, MoveFn move) {
+  __shared__ uint32_t wh[RS_WARPS][RS_RADIX];
+  __shared__ uint32_t gb[RS_RADIX];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < RS_WARPS * RS_RADIX; t += RS_THREADS) (&wh[0][0])[t] = 0;
+  for (int t = threadIdx.x; t < RS_RADIX; t += RS_THREADS) gb[t] = hist[(long long)t * ntiles + blockIdx.x];
+  __syncthreads();
+  long long base = (long long)blockIdx.x * RS_TILE + (long long)w * 32 * RS_ITEMS;
+  uint32_t dig[RS_ITEMS], rk[RS_ITEMS];
+  unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    long long i = base + k * 32 + lane;
+    uint32_t d = i < n ? key.digit(i, shift) : RS_RADIX;  // RS_RADIX: past the end
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = 0;
+    if (d < RS_RADIX) before = wh[w][d];
+    __syncwarp();
+    int leader = __ffs(peers) - 1;
+    if (d < RS_RADIX && lane == leader) wh[w][d] = before + __popc(peers);
+    __syncwarp();
+    dig[k] = d;
+    rk[k] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  // exclusive prefix across warps, per digit
+  for (int t = threadIdx.x; t < RS_RADIX; t += RS_THREADS) {
+    uint32_t run = 0;
+#pragma unroll
+    for (int q = 0; q < RS_WARPS; ++q) {
+      uint32_t c = wh[q][t];
+      wh[q][t] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < RS_ITEMS; ++k) {
+    long long i = base + k * 32 + lane;
+    if (i < n) move(i, (long long)gb[dig[k]] + wh[w][dig[k]] + rk[k]);
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scatter128(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo, const uint32_t* __restrict__ v,
+                    uint64_t* __restrict__ hi2, uint64_t* __restrict__ lo2, uint32_t* __restrict__ v2, long long n,
+                    int shift, const uint32_t* __restrict__ hist, int ntiles) {
+  Key128 key{hi, lo};
+  rs_scatter_body(key, n, shift, hist, ntiles, [&](long long i, long long dst) {
+    if (hi) hi2[dst] = hi[i];
+    lo2[dst] = lo[i];
+    v2[dst] = v[i];
+  });
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scatter32(const uint32_t* __restrict__ k, const uint32_t* __restrict__ v, uint32_t* __restrict__ k2,
+                   uint32_t* __restrict__ v2, long long n, int shift, const uint32_t* __restrict__ hist, int ntiles) {
+  Key32 key{k};
+  rs_scatter_body(key, n, shift, hist, ntiles, [&](long long i, long long dst) {
+    k2[dst] = k[i];
+    v2[dst] = v[i];
+  });
+}
+
+}  // namespace
+
+int scan_u32(uint32_t* data, long long n, uint32_t* total, Workspace& ws, cudaStream_t st) {
+  if (n <= 0) {
+    if (total) CSO_CUDA(cudaMemsetAsync(total, 0, sizeof(uint32_t), st));
+    return CSO_OK;
+  }
+  long long ntiles = cdiv(n, SCAN_TILE);
+  if (ntiles == 1) {
+    k_scan_single<<<1, 1024, 0, st>>>(data, n, total);
+    CSO_CUDA(cudaGetLastError());
+    return CSO_OK;
+  }
+  size_t mark = ws.off;
+  uint32_t* sums = ws.get<uint32_t>(ntiles);
+  if (!sums) {
+    cso_set_error("workspace exhausted in scan");
+    return CSO_ERR_BUDGET;
+  }
+  k_tile_sums<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(data, n, sums);
+  k_scan_single<<<1, 1024, 0, st>>>(sums, ntiles, total);
+  k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(data, n, sums);
+  CSO_CUDA(cudaGetLastError());
+  ws.off = mark;
+  return CSO_OK;
+}
+
+int radix_sort_128(uint64_t** khi, uint64_t** klo, uint32_t** val, uint64_t* khi_alt, uint64_t* klo_alt,
+                   uint32_t* val_alt, long long n, int bits, Workspace& ws, cudaStream_t st) {
+  if (n <= 1 || bits <= 0) return CSO_OK;
+  int ntiles = (int)cdiv(n, RS_TILE);
+  size_t mark = ws.off;
+  uint32_t* hist = ws.get<uint32_t>((size_t)ntiles * RS_RADIX);
+  if (!hist) {
+    cso_set_error("workspace exhausted in radix sort");
+    return CSO_ERR_BUDGET;
+  }
+  bool with_hi = bits > 64;
+  for (int shift = 0; shift < bits; shift += 8) {
+    Key128 key{with_hi ? *khi : nullptr, *klo};
+    k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(key, n, shift, hist, ntiles);
+    CSO_TRY(scan_u32(hist, (long long)ntiles * RS_RADIX, nullptr, ws, st));
+    k_rs_scatter128<<<ntiles, RS_THREADS, 0, st>>>(with_hi ? *khi : nullptr, *klo, *val, khi_alt, klo_alt, val_alt, n,
+                                                   shift, hist, ntiles);
+    CSO_CUDA(cudaGetLastError());
+    uint64_t* t1 = *khi; *khi = khi_alt; khi_alt = t1;
+    uint64_t* t2 = *klo; *klo = klo_alt; klo_alt = t2;
+    uint32_t* t3 = *val; *val = val_alt; val_alt = t3;
+  }
+  ws.off = mark;
+  return CSO_OK;
+}
+
+int radix_sort_32(uint32_t** key, uint32_t** val, uint32_t* key_alt, uint32_t* val_alt, long long n, int bits,
+                  Workspace& ws, cudaStream_t st) {
+  if (n <= 1 || bits <= 0) return CSO_OK;
+  int ntiles = (int)cdiv(n, RS_TILE);
+  size_t mark = ws.off;
+  uint32_t* hist = ws.get<uint32_t>((size_t)ntiles * RS_RADIX);
+  if (!hist) {
+    cso_set_error("workspace exhausted in radix sort");
+    return CSO_ERR_BUDGET;
+  }
+  for (int shift = 0; shift < bits; shift += 8) {
+    Key32 k{*key};
+    k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(k, n, shift, hist, ntiles);
+    CSO_TRY(scan_u32(hist, (long long)ntiles * RS_RADIX, nullptr, ws, st));
+    k_rs_scatter32<<<ntiles, RS_THREADS, 0, st>>>(*key, *val, key_alt, val_alt, n, shift, hist, ntiles);
+    CSO_CUDA(cudaGetLastError());
+    uint32_t* t1 = *key; *key = key_alt; key_alt = t1;
+    uint32_t* t2 = *val; *val = val_alt; val_alt = t2;
+  }
+  ws.off = mark;
+  return CSO_OK;
+}

@@ -1,0 +1,61 @@
+"""The C-ABI library loads, exports every entry point its header declares,
+and its host-side parameter derivation agrees bit for bit with the oracle's
+independent derivation (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle as O
+from paper_2110_11408_gb300 import cso
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(cso_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = cso.lib()
+    names = declared_functions()
+    assert {"cso_init", "cso_params_derive", "cso_find_groups", "cso_submit", "cso_poll", "cso_free"} <= names
+    for nm in names:
+        assert hasattr(L, nm), nm
+
+
+@pytest.mark.parametrize("u", [32768, 16384, 8192, 4096, 2048])
+@pytest.mark.parametrize("kw", [{}, dict(alpha=(7, 10)), dict(l_fof=0.30), dict(delta_L0=40.0),
+                                dict(delta_L1=258.2, delta_L2=1033.0, delta_L0=77.5)])
+def test_derived_parameters_match_oracle(u, kw):
+    p = cso.cso_params_default(u, **kw)
+    q = O.params(u, **kw)
+    for f in ("b2", "lfof2", "T_L0", "T_min_L1", "T_min_L2"):
+        assert getattr(p, f) == getattr(q, f), f
+    assert p.K_L1 == q.K_L1 and p.K_L2 == q.K_L2
+
+
+def test_invalid_parameters_rejected():
+    p = cso.cso_params_default(32768)
+    p.l_mean_grid = 32768.5
+    with pytest.raises(cso.CsoError):
+        cso.cso_params_derive(p)
+    p = cso.cso_params_default(32768)
+    p.grid_bits = 20
+    with pytest.raises(cso.CsoError):
+        cso.cso_params_derive(p)
+
+
+def test_struct_layout_matches_header():
+    # offsets of the ctypes mirror follow the C declaration order with natural alignment
+    assert ctypes.sizeof(cso.CsoParams) == 4 + 4 + 8 * 6 + 4 * 6 + 8 * 5 + 8 * 2
+    assert ctypes.sizeof(cso.CsoHalo) == 8 * 19
+    assert ctypes.sizeof(cso.CsoInput) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8
+    assert ctypes.sizeof(cso.CsoOutput) == 8 * 5 + 8 + 8 + 4 + 4

@@ -1,0 +1,211 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Integer outputs (kernel sums, L0/L1/L2 labels, nucleus ids, N, R^2) must be
+bit-identical; FP64 halo statistics (centres of mass, R_Delta) within 1e-9
+relative (the path accumulates them exactly in integers, so they agree far
+below the 1e-6 bar).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2110_11408_gb300 import cso, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+BOX = 1 << 21
+U64 = 32768
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = cso.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_stress():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = cso.Context(0, flags=cso.FLAG_SELECT_STRESS)
+    yield c
+    c.close()
+
+
+def both_params(u, **kw):
+    return cso.cso_params_default(u, **kw), O.params(u, **kw)
+
+
+def assert_same(g, o, n_sample_fp=None):
+    for k in ("sigma", "l0", "l1", "l2"):
+        a, b = g[k], o[k]
+        if not np.array_equal(a, b):
+            bad = np.nonzero(a != b)[0]
+            raise AssertionError("%s differs at %d of %d entries, first %s: gpu %s oracle %s"
+                                 % (k, bad.size, a.size, bad[:5], a[bad[:5]], b[bad[:5]]))
+    H, Ho = g["halos"], o["halos"]
+    assert len(H) == len(Ho), (len(H), len(Ho))
+    for f in ("nucleus_id", "N", "R2", "l2max_id", "l2max_N", "l2_top5_N", "n_l2", "l0_id"):
+        assert np.array_equal(H[f], Ho[f]), f
+    for f in ("com", "l2max_com", "R_delta"):
+        np.testing.assert_allclose(H[f], Ho[f], rtol=1e-9, atol=1e-9 * BOX)
+
+
+def run_both(ctx, pos, ids, u=U64, on_device=True, **kw):
+    pg, po = both_params(u, **kw)
+    g = ctx.find_groups(pos, ids, pg, on_device=on_device)
+    o = O.find_groups(pos, ids, po)
+    return g, o
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_patch_across_periodic_corner(ctx, seed):
+    pos, ids, _ = synth.patch(extent=16.0, lo=-8.0, seed=seed)
+    g, o = run_both(ctx, pos, ids)
+    assert_same(g, o)
+    assert o["stats"]["l1_nuclei"] > 5
+
+
+def test_patch_select_stress(ctx_stress):
+    """Tiny select tiles force every branch of the radius search (window
+    narrowing, single-value bins, bins without the answer, exhaustion)."""
+    for seed in (4, 5):
+        pos, ids, _ = synth.patch(extent=18.0, lo=-3.0, seed=seed, nmax=4000)
+        g, o = run_both(ctx_stress, pos, ids)
+        assert_same(g, o)
+
+
+def test_tiny_box_full_parity(ctx):
+    """Box 64 l_mean, 262,144 particles, ~850 NFW haloes: every output."""
+    pos, ids, meta = synth.tiny()
+    g, o = run_both(ctx, pos, ids)
+    assert_same(g, o)
+    st = ctx.stats()
+    assert st["dense"] == o["stats"]["dense"]
+    assert st["l0_groups"] == o["stats"]["l0_groups"]
+    assert st["l1_nuclei"] == o["stats"]["l1_nuclei"]
+    assert st["l2_nuclei"] == o["stats"]["l2_nuclei"]
+    assert st["l1_work"] == o["stats"]["l1_work"]
+
+
+def test_tiny_box_select_stress(ctx_stress):
+    pos, ids, meta = synth.tiny()
+    g, o = run_both(ctx_stress, pos, ids)
+    assert_same(g, o)
+
+
+def test_host_buffers_match_device_buffers(ctx):
+    pos, ids, _ = synth.patch(extent=20.0, lo=30.0, seed=7)
+    p, _ = both_params(U64)
+    a = ctx.find_groups(pos, ids, p, on_device=True)
+    b = ctx.find_groups(pos, ids, p, on_device=False)
+    for k in ("sigma", "l0", "l1", "l2"):
+        assert np.array_equal(a[k], b[k])
+    assert np.array_equal(a["halos"], b["halos"])
+
+
+def test_input_order_does_not_matter(ctx):
+    pos, ids, _ = synth.patch(extent=16.0, lo=10.0, seed=8)
+    p, _ = both_params(U64)
+    a = ctx.find_groups(pos, ids, p)
+    perm = np.random.default_rng(0).permutation(len(pos))
+    b = ctx.find_groups(pos[perm], ids[perm], p)
+    for k in ("sigma", "l0", "l1", "l2"):
+        assert np.array_equal(a[k][perm], b[k])
+    assert np.array_equal(a["halos"], b["halos"])
+
+
+@pytest.mark.parametrize("kw", [dict(alpha=(7, 10)), dict(alpha=(9, 10)), dict(l_fof=0.30),
+                                dict(delta_L0=40.0), dict(roche=(1, 1)), dict(include_self=1),
+                                dict(np_min_L1=1)])
+def test_parameter_variants(ctx, kw):
+    pos, ids, _ = synth.patch(extent=16.0, lo=-8.0, seed=9)
+    g, o = run_both(ctx, pos, ids, **kw)
+    assert_same(g, o)
+
+
+def test_box_sizes(ctx):
+    """Other grids: box 128 (u = 16384) and box 256 (u = 8192) patches."""
+    for side in (128, 256):
+        pos, ids, _ = synth.patch(extent=14.0, lo=-5.0, side=side, seed=10)
+        g, o = run_both(ctx, pos, ids, u=BOX // side)
+        assert_same(g, o)
+
+
+def test_edge_cases(ctx):
+    p, po = both_params(U64)
+    # empty input
+    e = ctx.find_groups(np.zeros((0, 3), np.int32), np.zeros(0, np.uint64), p)
+    assert e["n_halos"] == 0 and all(e[k].size == 0 for k in ("l0", "l1", "l2", "sigma"))
+    # one particle
+    one = ctx.find_groups(np.array([[5, 6, 7]], np.int32), np.array([42], np.uint64), p)
+    assert one["sigma"][0] == 0 and one["l0"][0] == cso.NO_GROUP
+    # many particles on one spot: equal Sigma everywhere, ties broken by id
+    pos = np.full((300, 3), 1000, np.int32)
+    ids = np.random.default_rng(1).permutation(300).astype(np.uint64) + 7
+    g, o = run_both(ctx, pos, ids, np_min_L1=1)
+    assert_same(g, o)
+    # a cubic lattice (many equal distances), straddling the box corner
+    lat, lid, _ = synth.lattice_ball(int(0.06 * U64), 150, [0, 0, 0])
+    g, o = run_both(ctx, lat, lid, np_min_L1=1)
+    assert_same(g, o)
+
+
+def test_rejects_positions_outside_grid(ctx):
+    p, _ = both_params(U64)
+    pos = np.array([[1, 2, 3], [BOX, 0, 0]], np.int32)
+    with pytest.raises(cso.CsoError) as e:
+        ctx.find_groups(pos, np.arange(2, dtype=np.uint64), p)
+    assert e.value.rc == cso.CSO_ERR_ARG
+
+
+def test_capacity_error_reports_needed_rows(ctx):
+    pos, ids, _ = synth.patch(extent=16.0, lo=-8.0, seed=1)
+    p, _ = both_params(U64, np_min_L1=1)
+    b = cso.Buffers(pos, ids, on_device=False, halo_cap=1)
+    rc = cso.lib().cso_find_groups(ctx.h, b.cin, p, b.cout)
+    assert rc == cso.CSO_ERR_CAPACITY and b.cout.n_halos > 1
+
+
+def test_medium_box_sampled_parity(ctx):
+    """Box 256 l_mean, 16.8M particles (the benchmark workload), in the
+    benchmark's launch configuration: kernel sums of 3000 sampled particles,
+    L0 consistency of sampled dense particles, and L1/L2 labels and catalogue
+    rows of 40 sampled L0 groups, each recomputed by the oracle on exactly
+    its own members (their kernel sums from the oracle on the full box)."""
+    from scipy.spatial import cKDTree
+    pos, ids, meta = synth.medium()
+    p, po = both_params(meta["u"], np_min_L1=1)
+    g = ctx.find_groups(pos, ids, p)
+    rng = np.random.default_rng(3)
+    n = len(pos)
+    sample = rng.choice(n, 3000, replace=False)
+    assert np.array_equal(g["sigma"][sample], O.density_at(pos, po, sample))
+    dense = g["sigma"] > po.T_L0
+    assert np.all((g["l0"] != cso.NO_GROUP) == dense)
+    tree = cKDTree(pos.astype(np.float64), boxsize=float(BOX))
+    ds = sample[dense[sample]]
+    for i, nb in zip(ds, tree.query_ball_point(pos[ds].astype(np.float64), np.sqrt(po.lfof2) - 1e-6)):
+        nb = np.asarray(nb)
+        nb = nb[dense[nb]]
+        d2 = (((pos[nb].astype(np.int64) - pos[i] + BOX // 2) % BOX - BOX // 2) ** 2).sum(1)
+        assert np.all(g["l0"][nb[d2 < po.lfof2]] == g["l0"][i])
+    groups, counts = np.unique(g["l0"][dense], return_counts=True)
+    big = groups[counts >= 200]
+    pick = np.concatenate([rng.choice(big, 20, replace=False), rng.choice(groups, 20, replace=False)])
+    for gid in pick:
+        m = np.nonzero(g["l0"] == gid)[0]
+        sig = O.density_at(pos, po, m)
+        assert np.array_equal(sig, g["sigma"][m])
+        l1, l2, halos, _ = O.compaso(pos[m], ids[m], sig, g["l0"][m], po)
+        assert np.array_equal(l1, g["l1"][m])
+        assert np.array_equal(l2, g["l2"][m])
+        mine = g["halos"][np.isin(g["halos"]["nucleus_id"], halos["nucleus_id"])]
+        assert len(mine) == len(halos)
+        for f in ("nucleus_id", "N", "R2", "l2max_id", "l2max_N", "l2_top5_N", "n_l2", "l0_id"):
+            assert np.array_equal(mine[f], halos[f]), f
+        np.testing.assert_allclose(mine["com"], halos["com"], rtol=1e-9, atol=1e-9 * BOX)
