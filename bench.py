@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "medium": dict(desc="medium box: side 256 l_mean, 16,777,216 particles, 40% background, 60% NFW haloes "
                         "N in [20, 2e5] (slope -1.9, c in [4, 12]), 10% with satellites"),
+    "medium128": dict(desc="the medium recipe in a side-128 box: 2,097,152 particles (profiling size)"),
     "tiny": dict(desc="tiny box: side 64 l_mean, 262,144 particles, 50% background, 50% NFW haloes N in "
                       "[20, 2e4]"),
 }
@@ -109,6 +110,8 @@ def make_workload(name, seed_offset):
         return synth.medium(seed=synth.SEED0 + 1 + 1000 * seed_offset)
     if name == "tiny":
         return synth.tiny(seed=synth.SEED0 + 1000 * seed_offset)
+    if name == "medium128":
+        return synth.medium_sample(side=128, seed=synth.SEED0 + 11 + 1000 * seed_offset)
     raise SystemExit("unknown workload " + name)
 
 

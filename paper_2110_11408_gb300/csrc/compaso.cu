@@ -292,17 +292,24 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
       for (int b = from + tid; b < NB; b += blockDim.x)
         if (S.cnt[b] && pred(base + S.clo[b], S.dmx[b], c)) atomicMin(&S.best, b);
       __syncthreads();
-      int b = S.best;
+      // read the chosen bin before the barrier: the next window pass rewrites it
+      const int b = S.best;
+      unsigned long long lo = 0, hi = 0, cb = 0;
+      unsigned cntb = 0;
+      if (b < NB) {
+        lo = S.dmn[b];
+        hi = S.dmx[b];
+        cb = base + S.clo[b];
+        cntb = S.cnt[b];
+      }
       __syncthreads();
       if (b == NB) break;  // nothing in this window
-      unsigned long long lo = S.dmn[b], hi = S.dmx[b];
-      unsigned long long cb = base + S.clo[b];
       if (lo == hi) {
         // one distinct value: its enclosed count is cb, and the bin test above
         // was the exact predicate at that value
         return (long long)lo;
       }
-      if (S.cnt[b] <= (unsigned)cap) {
+      if (cntb <= (unsigned)cap) {
         if (tid == 0) S.nlist = 0;
         __syncthreads();
         for (int j = tid; j < n; j += blockDim.x) {
