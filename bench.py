@@ -232,6 +232,7 @@ def main():
         torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
+    stats_t = cso.cso_last_stats(ctx.h)
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -297,7 +298,7 @@ def main():
         "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "n_particles": n,
                    "schedule": "batched" if args.batched else "plain", "l2_flush": "working set > L2 (inputs 336 MB, "
                    "cell table 1 GB)", "seed": meta["seed"]},
-        "e2e": e2e, "gpu_launches": None, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "stages_ms": stages,
         "counts": {k: stats[k] for k in ("dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows",
                                          "pairs_b", "l1_work", "l2_work", "workspace_bytes")},

@@ -178,7 +178,7 @@ int cso_stage_times(cso_ctx* ctx, double* ms, const char** names, int cap);
  * groups, [3] L1 nuclei, [4] L2 nuclei, [5] catalogue rows, [6] kernel pairs
  * with d < b2 (only with CSO_FLAG_COUNT_PAIRS), [7] sum over L1 nuclei of their
  * group size, [8] sum over L2 nuclei of their L1 halo size, [9] peak device
- * workspace bytes.  Returns the number written. */
+ * workspace bytes, [10] kernel launches.  Returns the number written. */
 int cso_last_stats(cso_ctx* ctx, int64_t* out, int cap);
 
 /* One-line description of the last error of this thread. */

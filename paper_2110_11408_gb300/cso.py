@@ -36,7 +36,7 @@ FLAG_COUNT_PAIRS = 8
 FLAG_SELECT_STRESS = 16
 
 STAT_NAMES = ["n", "dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows", "pairs_b", "l1_work",
-              "l2_work", "workspace_bytes"]
+              "l2_work", "workspace_bytes", "launches"]
 
 
 class CsoParams(ctypes.Structure):

@@ -15,6 +15,7 @@
 // errors
 // ---------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
+long long g_cso_launches = 0;
 
 void cso_set_error(const char* fmt, ...) {
   va_list ap;

@@ -168,12 +168,19 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || sigma[s] <= T_L0) return;
   int4 p = spos[s];
+  int rs = uf_root(parent, s);  // cached root of s; refreshed after every hook
   for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
     if ((int)t <= s) return true;  // every unordered pair once
     int4 q = spos[t];
     int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
     uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-    if (d < lfof2 && sigma[t] > T_L0) uf_unite(parent, s, (int)t);
+    if (d < lfof2 && sigma[t] > T_L0) {
+      int rt = uf_root(parent, (int)t);
+      if (rt != rs) {
+        uf_unite(parent, rs, rt);
+        rs = uf_root(parent, rs);
+      }
+    }
     return true;
   });
 }
@@ -191,40 +198,6 @@ __global__ void k_fof_finish(int* __restrict__ parent, int n, const long long* _
   int r = uf_root(parent, s);
   root[s] = r;
   atomicMin(&minid[r], (unsigned long long)sid[s]);
-}
-
-// peak[s] = 1 iff s has a group label, Sigma_s > T_min and no particle of the
-// same group within d < b2 comes before it in key order (Sigma desc, id asc).
-__global__ void __launch_bounds__(256) k_peak(CellGrid g, const int4* __restrict__ spos, int n,
-                                              const long long* __restrict__ sigma, const uint64_t* __restrict__ sid,
-                                              const int* __restrict__ label, long long T_min, uint32_t b2,
-                                              uint8_t* __restrict__ peak) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  int lab = label[s];
-  long long sg = sigma[s];
-  if (lab < 0 || sg <= T_min) {
-    peak[s] = 0;
-    return;
-  }
-  uint64_t id = sid[s];
-  int4 p = spos[s];
-  bool is_peak = true;
-  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
-    if ((int)t == s) return true;
-    int4 q = spos[t];
-    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
-    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-    if (d < b2 && label[t] == lab) {
-      long long st = sigma[t];
-      if (st > sg || (st == sg && sid[t] < id)) {
-        is_peak = false;
-        return false;
-      }
-    }
-    return true;
-  });
-  peak[s] = is_peak;
 }
 
 }  // namespace
@@ -259,12 +232,12 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint
   }
   CSO_CUDA(cudaMemsetAsync(start, 0, sizeof(uint32_t) * (ncell + 1), st));
   if (n > 0) {
-    k_cell_count<<<cdiv(n, 256), 256, 0, st>>>(pos, n, nc, key, rank, start, bad);
+    k_cell_count<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, n, nc, key, rank, start, bad);
     CSO_CUDA(cudaGetLastError());
   }
   CSO_TRY(scan_u32(start, ncell + 1, nullptr, ws, st));
   if (n > 0) {
-    k_cell_scatter<<<cdiv(n, 256), 256, 0, st>>>(pos, ids, n, key, rank, start, spos, sid);
+    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, key, rank, start, spos, sid);
     CSO_CUDA(cudaGetLastError());
   }
   ws.off = mark;
@@ -275,9 +248,9 @@ int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int i
                   unsigned long long* pairs, cudaStream_t st) {
   if (n <= 0) return CSO_OK;
   if (pairs)
-    k_density<true><<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, pairs);
+    k_density<true><<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, pairs);
   else
-    k_density<false><<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, nullptr);
+    k_density<false><<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, nullptr);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;
 }
@@ -285,18 +258,10 @@ int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int i
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
               const uint64_t* sid, int* parent, int* root, unsigned long long* minid, cudaStream_t st) {
   if (n <= 0) return CSO_OK;
-  k_fof_init<<<cdiv(n, 256), 256, 0, st>>>(parent, n);
-  k_fof_link<<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, sigma, T_L0, lfof2, parent);
+  k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
+  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, sigma, T_L0, lfof2, parent);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
-  k_fof_finish<<<cdiv(n, 256), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
-  CSO_CUDA(cudaGetLastError());
-  return CSO_OK;
-}
-
-int cells_peak(const CellGrid& g, const int4* spos, int n, const long long* sigma, const uint64_t* sid,
-               const int* label, long long T_min, uint32_t b2, uint8_t* peak, cudaStream_t st) {
-  if (n <= 0) return CSO_OK;
-  k_peak<<<cdiv(n, 256), 256, 0, st>>>(g, spos, n, sigma, sid, label, T_min, b2, peak);
+  k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;
 }

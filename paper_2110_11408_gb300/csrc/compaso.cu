@@ -14,6 +14,7 @@
 //           eligibility marking.
 #include <float.h>
 
+#include "cells.cuh"
 #include "compaso.cuh"
 
 namespace {
@@ -355,20 +356,69 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
   return r;
 }
 
+// Step 2's density criterion for member e of the segment: no particle of the
+// same group (label) within d < b2 comes before it in key order.  The block
+// scans the 27-cell stencil of e cooperatively and stops at the first beater.
+__device__ bool block_is_peak(const LevelArgs& a, uint32_t se, int glabel, int* beaten, StencilRun* runs,
+                              unsigned* run_off, int* nrun) {
+  const int tid = threadIdx.x;
+  const int4 p = a.spos[se];
+  const long long sp = a.ssig[se];
+  const uint64_t idp = a.sid[se];
+  if (tid == 0) {
+    int r = stencil_runs(a.grid, p.x, p.y, p.z, runs);
+    unsigned acc = 0;
+    for (int i = 0; i < r; ++i) {
+      run_off[i] = acc;
+      acc += runs[i].hi - runs[i].lo;
+    }
+    run_off[r] = acc;
+    *nrun = r;
+    *beaten = 0;
+  }
+  __syncthreads();
+  const int r = *nrun;
+  const unsigned total = run_off[r];
+  for (unsigned f0 = 0; f0 < total; f0 += blockDim.x) {
+    unsigned f = f0 + tid;
+    if (f < total) {
+      int k = 0;
+      while (run_off[k + 1] <= f) ++k;
+      const StencilRun R = runs[k];
+      uint32_t t = R.lo + (f - run_off[k]);
+      if (t != se) {
+        int4 q = a.spos[t];
+        int dx = R.qx - q.x, dy = R.qy - q.y, dz = R.qz - q.z;
+        uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+        if (d < a.b2 && a.slab[t] == glabel) {
+          long long st = a.ssig[t];
+          if (st > sp || (st == sp && a.sid[t] < idp)) *beaten = 1;
+        }
+      }
+    }
+    if (__syncthreads_or(*beaten)) break;
+  }
+  bool peak = *beaten == 0;
+  __syncthreads();
+  return peak;
+}
+
 __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
   __shared__ SelShared S;
-  __shared__ int sP, sNc;
+  __shared__ StencilRun runs[18];
+  __shared__ unsigned run_off[19];
+  __shared__ int sP, sE, sNrun, sBeaten;
   const int seg = blockIdx.x;
   const unsigned base = a.seg_off[seg];
   const int n = (int)(a.seg_off[seg + 1] - base);
   const int tid = threadIdx.x;
   const int4* epos = a.epos + base;
   const long long* esig = a.esig + base;
+  const uint32_t* egs = a.egs + base;
   int* eslot = a.eslot + base;
   long long* edold = a.edold + base;
   uint8_t* einel = a.einel + base;
   long long* ed = a.ed + base;
-  uint32_t* ecand = a.ecand + base;
 
   for (int j = tid; j < n; j += blockDim.x) {
     eslot[j] = -1;
@@ -383,28 +433,39 @@ __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
       else hi = mid;
     }
     sP = lo;
-    sNc = 0;
   }
   __syncthreads();
   const int P = sP;
-  // ordered list of local peaks among them (step 2's density criterion)
-  for (int c0 = 0; c0 < P; c0 += blockDim.x) {
-    int j = c0 + tid;
-    unsigned f = (j < P && a.epeak[base + j]) ? 1u : 0u;
-    unsigned excl;
-    unsigned tot = block_scan(f, excl, S.sw);
-    if (f) ecand[sNc + excl] = (uint32_t)j;
-    __syncthreads();
-    if (tid == 0) sNc += tot;
-    __syncthreads();
-  }
-  const int ncand = sNc;
+  const int glabel = a.slab[egs[0]];  // every member carries the group's label
   const long long anum2 = (long long)a.alpha_num * a.alpha_num, aden2 = (long long)a.alpha_den * a.alpha_den;
   int nn = 0;
-  for (int k = 0; k < ncand; ++k) {
-    const int cidx = (int)ecand[k];
-    if (einel[cidx]) continue;  // step 2: only eligible particles seed nuclei
-    const int4 pc = epos[cidx];
+  int c = 0;
+  while (c < P) {
+    // step 2: the next eligible candidate in key order
+    if (tid == 0) sE = P;
+    __syncthreads();
+    for (int c0 = c; c0 < P; c0 += 4 * LV_THREADS) {
+      int first = P;
+      for (int q = 0; q < 4; ++q) {
+        int j = c0 + tid * 4 + q;
+        if (j < P && !einel[j]) {
+          first = j;
+          break;
+        }
+      }
+      if (__syncthreads_or(first < P)) {
+        if (first < P) atomicMin(&sE, first);
+        __syncthreads();
+        break;
+      }
+    }
+    const int e = sE;
+    __syncthreads();
+    if (e >= P) break;
+    c = e + 1;
+    // ... which must also be denser than every group member within b
+    if (!block_is_peak(a, egs[e], glabel, &sBeaten, runs, run_off, &sNrun)) continue;
+    const int4 pc = epos[e];
     const long long R2 = r_search(epos, ed, n, pc, a.pc, S, a.small_n, a.cap, a.nb);
     // steps 1 and 3
     for (int j = tid; j < n; j += blockDim.x) {
@@ -427,7 +488,7 @@ __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
       if ((__int128)aden2 * d < (__int128)anum2 * R2) einel[j] = 1;
     }
     if (tid == 0) {
-      a.nuc_member[base + nn] = (uint32_t)cidx;
+      a.nuc_member[base + nn] = (uint32_t)e;
       a.nuc_R2[base + nn] = R2;
     }
     ++nn;
@@ -464,7 +525,7 @@ __global__ void k_level_halo(const uint32_t* __restrict__ seg_off, const uint32_
 
 int level_run(const LevelArgs& a, cudaStream_t st) {
   if (a.nseg <= 0) return CSO_OK;
-  k_level<<<a.nseg, LV_THREADS, 0, st>>>(a);
+  k_level<<<CL(a.nseg), LV_THREADS, 0, st>>>(a);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;
 }
@@ -473,7 +534,7 @@ int level_halo(int nseg, const uint32_t* seg_off, const uint32_t* nnuc, const ui
                const uint32_t* nuc_member, const long long* nuc_R2, int* ehalo, uint32_t* hnuc, long long* hR2,
                uint32_t* hseg, cudaStream_t st) {
   if (nseg <= 0) return CSO_OK;
-  k_level_halo<<<nseg, 256, 0, st>>>(seg_off, nnuc, hbase, eslot, nuc_member, nuc_R2, ehalo, hnuc, hR2, hseg);
+  k_level_halo<<<CL(nseg), 256, 0, st>>>(seg_off, nnuc, hbase, eslot, nuc_member, nuc_R2, ehalo, hnuc, hR2, hseg);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;
 }

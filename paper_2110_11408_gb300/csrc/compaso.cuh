@@ -1,6 +1,6 @@
 // CompaSO level kernels (compaso.cu).
 #pragma once
-#include "cso_internal.cuh"
+#include "cells.cuh"
 
 // constants of the exact predicate n^2 u^6 < K d^3
 struct PredConst {
@@ -18,7 +18,7 @@ struct LevelArgs {
   const uint32_t* seg_off;  // nseg + 1 offsets into the element arrays
   const int4* epos;         // member positions, key order within a segment
   const long long* esig;    // kernel sums (descending within a segment)
-  const uint8_t* epeak;     // local-peak flags
+  const uint32_t* egs;      // cell-sorted index of each member
   long long T_min;
   PredConst pc;
   int alpha_num, alpha_den, roche_num, roche_den;
@@ -26,7 +26,13 @@ struct LevelArgs {
   long long* edold;         // scratch: squared distance to the current nucleus
   uint8_t* einel;           // scratch: ineligible flags
   long long* ed;            // scratch: distances to the nucleus being processed
-  uint32_t* ecand;          // scratch: candidate list
+  // cell-sorted particle data for the local-peak test of step 2
+  CellGrid grid;
+  const int4* spos;
+  const long long* ssig;
+  const uint64_t* sid;
+  const int* slab;          // group label per cell-sorted particle (-1: none)
+  uint32_t b2;
   uint32_t* nuc_member;     // out: [seg_off + q] member offset of nucleus q
   long long* nuc_R2;        // out: [seg_off + q] its squared radius
   uint32_t* nnuc;           // out: nuclei per segment

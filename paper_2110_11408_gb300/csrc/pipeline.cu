@@ -4,9 +4,9 @@
 //   density  Sigma per particle (Eq. 1)
 //   fof      L0 groups over dense particles (Sec. 2.2.1)
 //   gather   dense particles sorted by (L0 group, Sigma desc, id asc)
-//   peak1    local-peak flags within L0 groups (step 2)
-//   level1   CompaSO L1, block per L0 group (steps 1-4)
-//   prep2    members of each L1 halo in key order, peak flags within L1
+//   level1   CompaSO L1, block per L0 group (steps 1-4; the local-peak test
+//            of step 2 runs inside, only for eligible candidates)
+//   prep2    members of each L1 halo in key order and their L1 labels
 //   level2   CompaSO L2, block per L1 halo
 //   output   labels in input order, per-halo statistics, catalogue
 #include <string.h>
@@ -35,14 +35,39 @@ __global__ void k_flags(const int* __restrict__ root, int n, uint32_t* __restric
   rflag[s] = r == s;
 }
 
-__global__ void k_compact_dense(const int* __restrict__ root, int n, const uint32_t* __restrict__ dscan,
-                                const long long* __restrict__ sigma, const uint64_t* __restrict__ sid,
-                                uint32_t* __restrict__ dl, Meta* meta) {
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
+  for (int o = 16; o; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  v = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v = sh[i] > v ? sh[i] : v;
+  __syncthreads();
+  return v;
+}
+
+// compact the dense particles; block maxima of Sigma and id, one atomic per block
+__global__ void __launch_bounds__(256) k_compact_dense(const int* __restrict__ root, int n,
+                                                       const uint32_t* __restrict__ dscan,
+                                                       const long long* __restrict__ sigma,
+                                                       const uint64_t* __restrict__ sid, uint32_t* __restrict__ dl,
+                                                       Meta* meta) {
+  __shared__ unsigned long long sh[8];
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n || root[s] < 0) return;
-  dl[dscan[s]] = (uint32_t)s;
-  atomicMax(&meta->sigma_max, (unsigned long long)sigma[s]);
-  atomicMax(&meta->id_max, (unsigned long long)sid[s]);
+  unsigned long long ms = 0, mid = 0;
+  if (s < n && root[s] >= 0) {
+    dl[dscan[s]] = (uint32_t)s;
+    ms = (unsigned long long)sigma[s];
+    mid = (unsigned long long)sid[s];
+  }
+  ms = block_max_u64(ms, sh);
+  mid = block_max_u64(mid, sh);
+  if (threadIdx.x == 0) {
+    atomicMax(&meta->sigma_max, ms);
+    atomicMax(&meta->id_max, mid);
+  }
 }
 
 // key = group | (Sigma_max - Sigma) | id, packed low to high: id, Sigma', group
@@ -94,12 +119,6 @@ __global__ void k_gather1(const uint32_t* __restrict__ val, int nd, const int4* 
   eid[k] = sid[s];
 }
 
-__global__ void k_gather_u8(const uint32_t* __restrict__ idx, int m, const uint8_t* __restrict__ src,
-                            uint8_t* __restrict__ dst) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < m) dst[k] = src[idx[k]];
-}
-
 __global__ void k_flag_assigned(const int* __restrict__ ehalo, int nd, uint32_t* __restrict__ f) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < nd) f[k] = ehalo[k] >= 0;
@@ -119,14 +138,13 @@ __global__ void k_compact_assigned(const int* __restrict__ ehalo, int nd, const 
 
 __global__ void k_gather2(const uint32_t* __restrict__ ek, int m, const int4* __restrict__ epos,
                           const long long* __restrict__ esig, const uint32_t* __restrict__ gs,
-                          const uint8_t* __restrict__ peak2, int4* __restrict__ epos2, long long* __restrict__ esig2,
-                          uint8_t* __restrict__ epeak2) {
+                          int4* __restrict__ epos2, long long* __restrict__ esig2, uint32_t* __restrict__ egs2) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   uint32_t k = ek[i];
   epos2[i] = epos[k];
   esig2[i] = esig[k];
-  epeak2[i] = peak2[gs[k]];
+  egs2[i] = gs[k];
 }
 
 __global__ void k_fill_u64(uint64_t* p, long long n, uint64_t v) {
@@ -309,7 +327,7 @@ int readback(cso_ctx* c, const void* dev, size_t bytes) {
   return CSO_OK;
 }
 
-#define G1(n) cdiv((n), 256), 256, 0, st
+#define G1(n) CL(cdiv((n), 256)), 256, 0, st
 
 }  // namespace
 
@@ -318,6 +336,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   const long long n = in->n;
   memset(c->stats, 0, sizeof(c->stats));
   c->stats[0] = n;
+  const long long launches0 = g_cso_launches;
   c->nstages = 0;
   out->n_halos = 0;
   if (n == 0) return CSO_OK;
@@ -420,7 +439,6 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   ALLOC(int4, epos, nd);
   ALLOC(long long, esig, nd);
   ALLOC(uint64_t, eid, nd);
-  ALLOC(uint8_t, epeak, nd);
   uint32_t* gs = kval;
   if (nd > 0) {
     k_make_keys<<<G1(nd)>>>(dl, nd, root, rscan, sigma, sid, hm.sigma_max, bits_id, bits_sig, khi, klo, kval);
@@ -434,19 +452,12 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
     CSO_CUDA(cudaGetLastError());
   }
 
-  // ---- peak1 ----
-  S.mark("peak1");
-  ALLOC(uint8_t, peak, n);
-  CSO_TRY(cells_peak(g, spos, N, sigma, sid, root, p->T_min_L1, (uint32_t)p->b2, peak, st));
-  if (nd > 0) k_gather_u8<<<G1(nd)>>>(gs, nd, peak, epeak);
-
   // ---- level1 ----
   S.mark("level1");
   ALLOC(int, eslot, nd);
   ALLOC(long long, edold, nd);
   ALLOC(uint8_t, einel, nd);
   ALLOC(long long, ed, nd);
-  ALLOC(uint32_t, ecand, nd);
   ALLOC(uint32_t, nucm, nd);
   ALLOC(long long, nucR2, nd);
   ALLOC(uint32_t, nnuc, G + 1);
@@ -455,7 +466,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   L1.seg_off = seg1;
   L1.epos = epos;
   L1.esig = esig;
-  L1.epeak = epeak;
+  L1.egs = gs;
   L1.T_min = p->T_min_L1;
   L1.pc = make_pred_const(p->K_L1, (long long)p->l_mean_grid);
   L1.alpha_num = p->alpha_num;
@@ -466,7 +477,12 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   L1.edold = edold;
   L1.einel = einel;
   L1.ed = ed;
-  L1.ecand = ecand;
+  L1.grid = g;
+  L1.spos = spos;
+  L1.ssig = sigma;
+  L1.sid = sid;
+  L1.slab = root;
+  L1.b2 = (uint32_t)p->b2;
   L1.nuc_member = nucm;
   L1.nuc_R2 = nucR2;
   L1.nnuc = nnuc;
@@ -511,12 +527,10 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
     k_seg_bounds32<<<G1(na)>>>(pk, na, H1, seg2);
     ek2 = pv;
   }
-  ALLOC(uint8_t, peak2, n);
-  CSO_TRY(cells_peak(g, spos, N, sigma, sid, lab1, p->T_min_L2, (uint32_t)p->b2, peak2, st));
   ALLOC(int4, epos2, na);
   ALLOC(long long, esig2, na);
-  ALLOC(uint8_t, epeak2, na);
-  if (na > 0) k_gather2<<<G1(na)>>>(ek2, na, epos, esig, gs, peak2, epos2, esig2, epeak2);
+  ALLOC(uint32_t, egs2, na);
+  if (na > 0) k_gather2<<<G1(na)>>>(ek2, na, epos, esig, gs, epos2, esig2, egs2);
   CSO_CUDA(cudaGetLastError());
 
   // ---- level2 ----
@@ -530,7 +544,8 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   L2.seg_off = seg2;
   L2.epos = epos2;
   L2.esig = esig2;
-  L2.epeak = epeak2;
+  L2.egs = egs2;
+  L2.slab = lab1;
   L2.T_min = p->T_min_L2;
   L2.pc = make_pred_const(p->K_L2, (long long)p->l_mean_grid);
   L2.eslot = eslot2;
@@ -538,7 +553,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   L2.nuc_R2 = nucR22;
   L2.nnuc = nnuc2;
   L2.work = &meta->work2;
-  CSO_TRY(level_run(L2, st));  // edold / einel / ed / ecand are reused (na <= nd)
+  CSO_TRY(level_run(L2, st));  // edold / einel / ed are reused (na <= nd)
 
   // ---- output ----
   S.mark("output");
@@ -587,7 +602,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   ALLOC(uint32_t, keep, H1 + 1);
   int nrows = 0;
   if (H1 > 0) {
-    k_summary<<<H1, 256, 0, st>>>(seg2, epos2, ehalo2, ek2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2,
+    k_summary<<<CL(H1), 256, 0, st>>>(seg2, epos2, ehalo2, ek2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2,
                                    h2size, 1.0 / p->l_mean_grid, p->np_min_L1, rows, keep);
     CSO_CUDA(cudaGetLastError());
     ALLOC(uint32_t, kscan, H1 + 1);
@@ -631,6 +646,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   c->stats[7] = (int64_t)hm.work1;
   c->stats[8] = (int64_t)hm.work2;
   c->stats[9] = (int64_t)ws.peak;
+  c->stats[10] = g_cso_launches - launches0;
 #undef ALLOC
   if (nrows > out->halo_cap) {
     cso_set_error("catalogue has %d rows, halo_cap is %lld", nrows, (long long)out->halo_cap);

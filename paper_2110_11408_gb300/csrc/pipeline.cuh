@@ -6,7 +6,7 @@
 #include "cso_internal.cuh"
 
 #define CSO_MAX_STAGES 16
-#define CSO_NSTATS 10
+#define CSO_NSTATS 11
 // device workspace per particle (all stages, worst case), bytes
 #define CSO_BYTES_PER_PARTICLE 440
 

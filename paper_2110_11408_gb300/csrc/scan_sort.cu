@@ -220,7 +220,7 @@ int scan_u32(uint32_t* data, long long n, uint32_t* total, Workspace& ws, cudaSt
   }
   long long ntiles = cdiv(n, SCAN_TILE);
   if (ntiles == 1) {
-    k_scan_single<<<1, 1024, 0, st>>>(data, n, total);
+    k_scan_single<<<CL(1), 1024, 0, st>>>(data, n, total);
     CSO_CUDA(cudaGetLastError());
     return CSO_OK;
   }
@@ -230,9 +230,9 @@ int scan_u32(uint32_t* data, long long n, uint32_t* total, Workspace& ws, cudaSt
     cso_set_error("workspace exhausted in scan");
     return CSO_ERR_BUDGET;
   }
-  k_tile_sums<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(data, n, sums);
-  k_scan_single<<<1, 1024, 0, st>>>(sums, ntiles, total);
-  k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(data, n, sums);
+  k_tile_sums<<<CL((unsigned)ntiles), SCAN_THREADS, 0, st>>>(data, n, sums);
+  k_scan_single<<<CL(1), 1024, 0, st>>>(sums, ntiles, total);
+  k_scan_tiles<<<CL((unsigned)ntiles), SCAN_THREADS, 0, st>>>(data, n, sums);
   CSO_CUDA(cudaGetLastError());
   ws.off = mark;
   return CSO_OK;
@@ -251,9 +251,9 @@ int radix_sort_128(uint64_t** khi, uint64_t** klo, uint32_t** val, uint64_t* khi
   bool with_hi = bits > 64;
   for (int shift = 0; shift < bits; shift += 8) {
     Key128 key{with_hi ? *khi : nullptr, *klo};
-    k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(key, n, shift, hist, ntiles);
+    k_rs_hist<<<CL(ntiles), RS_THREADS, 0, st>>>(key, n, shift, hist, ntiles);
     CSO_TRY(scan_u32(hist, (long long)ntiles * RS_RADIX, nullptr, ws, st));
-    k_rs_scatter128<<<ntiles, RS_THREADS, 0, st>>>(with_hi ? *khi : nullptr, *klo, *val, khi_alt, klo_alt, val_alt, n,
+    k_rs_scatter128<<<CL(ntiles), RS_THREADS, 0, st>>>(with_hi ? *khi : nullptr, *klo, *val, khi_alt, klo_alt, val_alt, n,
                                                    shift, hist, ntiles);
     CSO_CUDA(cudaGetLastError());
     uint64_t* t1 = *khi; *khi = khi_alt; khi_alt = t1;
@@ -276,9 +276,9 @@ int radix_sort_32(uint32_t** key, uint32_t** val, uint32_t* key_alt, uint32_t* v
   }
   for (int shift = 0; shift < bits; shift += 8) {
     Key32 k{*key};
-    k_rs_hist<<<ntiles, RS_THREADS, 0, st>>>(k, n, shift, hist, ntiles);
+    k_rs_hist<<<CL(ntiles), RS_THREADS, 0, st>>>(k, n, shift, hist, ntiles);
     CSO_TRY(scan_u32(hist, (long long)ntiles * RS_RADIX, nullptr, ws, st));
-    k_rs_scatter32<<<ntiles, RS_THREADS, 0, st>>>(*key, *val, key_alt, val_alt, n, shift, hist, ntiles);
+    k_rs_scatter32<<<CL(ntiles), RS_THREADS, 0, st>>>(*key, *val, key_alt, val_alt, n, shift, hist, ntiles);
     CSO_CUDA(cudaGetLastError());
     uint32_t* t1 = *key; *key = key_alt; key_alt = t1;
     uint32_t* t2 = *val; *val = val_alt; val_alt = t2;
