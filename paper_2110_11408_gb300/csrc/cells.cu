@@ -24,7 +24,7 @@ __device__ __forceinline__ int wrap_cell(int c, int nc, int& shift) {
   return c;
 }
 
-__device__ __forceinline__ int cell_of(int x, int nc) { return (int)(((unsigned long long)(unsigned)x * (unsigned)nc) >> 21); }
+__device__ __forceinline__ int cell_of(int x, int nc) { return cell_coord(x, nc); }
 
 // Visit every sorted index t whose cell is in the 27-stencil of the query;
 // f(t, xq, yq, zq) receives the shifted query coordinates.  f returns false to stop.
@@ -92,34 +92,82 @@ __global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* 
   sid[dst] = ids[i];
 }
 
-// Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2)
-template <bool COUNT>
+__device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_t b2) {
+  const int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
+  const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+  return b2 - (d < b2 ? d : b2);  // b2 - d inside the kernel support, else 0
+}
+
+__device__ __forceinline__ unsigned long long sum_run(const int4* __restrict__ spos, uint32_t t, uint32_t e, int xq,
+                                                      int yq, int zq, uint32_t b2) {
+  unsigned long long acc = 0;
+  // four independent loads in flight; four terms < 2^28 each fit a uint32
+  for (; t + 4 <= e; t += 4) {
+    const int4 q0 = spos[t], q1 = spos[t + 1], q2 = spos[t + 2], q3 = spos[t + 3];
+    acc += kern(q0, xq, yq, zq, b2) + kern(q1, xq, yq, zq, b2) + kern(q2, xq, yq, zq, b2) +
+           kern(q3, xq, yq, zq, b2);
+  }
+  for (; t < e; ++t) acc += kern(spos[t], xq, yq, zq, b2);
+  return acc;
+}
+
+// Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2).
+// Away from the x faces of the box the 9 rows of the stencil are looked up
+// first, so the 18 table loads are in flight together; particles in the
+// first or last x cell (a row that wraps) take the general stencil walk.
 __global__ void __launch_bounds__(256) k_density(CellGrid g, const int4* __restrict__ spos, int n, uint32_t b2,
-                                                 int include_self, long long* __restrict__ sigma,
-                                                 unsigned long long* __restrict__ pairs) {
+                                                 int include_self, long long* __restrict__ sigma) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  int4 p = spos[s];
+  const int4 p = spos[s];
+  const int nc = g.nc;
+  const int cx = cell_of(p.x, nc), cy = cell_of(p.y, nc), cz = cell_of(p.z, nc);
   unsigned long long acc = 0;
-  unsigned cnt = 0;
-  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
-    int4 q = spos[t];
-    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
-    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-    uint32_t m = d < b2 ? d : b2;
-    acc += b2 - m;
-    if (COUNT) cnt += d < b2;
-    return true;
-  });
+  if (cx >= 1 && cx + 1 < nc) {
+    uint32_t lo[9], hi[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      int sz, sy;
+      const int zz = wrap_cell(cz + r / 3 - 1, nc, sz);
+      const int yy = wrap_cell(cy + r % 3 - 1, nc, sy);
+      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
+      lo[r] = row[cx - 1];
+      hi[r] = row[cx + 2];
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      int sz, sy;
+      wrap_cell(cz + r / 3 - 1, nc, sz);
+      wrap_cell(cy + r % 3 - 1, nc, sy);
+      acc += sum_run(spos, lo[r], hi[r], p.x, p.y + sy, p.z + sz, b2);
+    }
+  } else {
+    for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+      acc += kern(spos[t], xq, yq, zq, b2);
+      return true;
+    });
+  }
   // the particle met itself once at d = 0
   if (!include_self) acc -= b2;
   sigma[s] = (long long)acc;
-  if (COUNT) {
+}
+
+// number of ordered pairs j != s with d < b2 (the algorithmic work of the
+// density pass; a separate diagnostic launch)
+__global__ void __launch_bounds__(256) k_count_pairs(CellGrid g, const int4* __restrict__ spos, int n, uint32_t b2,
+                                                     unsigned long long* __restrict__ pairs) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned cnt = 0;
+  if (s < n) {
+    const int4 p = spos[s];
+    for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+      cnt += kern(spos[t], xq, yq, zq, b2) != 0;
+      return true;
+    });
     cnt -= 1;  // the particle itself
-    unsigned mask = __activemask();
-    unsigned tot = __reduce_add_sync(mask, cnt);
-    if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(pairs, (unsigned long long)tot);
   }
+  unsigned tot = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0) atomicAdd(pairs, (unsigned long long)tot);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,29 +205,58 @@ __device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
   }
 }
 
-__global__ void k_fof_init(int* __restrict__ parent, int n) {
+// parent[s] = s for dense particles, -1 for the rest (one load answers both)
+__global__ void k_fof_init(int* __restrict__ parent, int n, const long long* __restrict__ sigma, long long T_L0) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) parent[s] = s;
+  if (s < n) parent[s] = sigma[s] > T_L0 ? s : -1;
 }
 
-__global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __restrict__ spos, int n,
-                                                  const long long* __restrict__ sigma, long long T_L0,
-                                                  uint32_t lfof2, int* __restrict__ parent) {
+// Sampling round (the idea of Afforest, Sutton et al. 2018): hook every dense
+// particle to its first two linked neighbours.  In dense regions this already
+// joins almost every particle to its final component.
+__global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __restrict__ spos, int n,
+                                                    uint32_t lfof2, int* __restrict__ parent) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n || sigma[s] <= T_L0) return;
+  if (s >= n || parent[s] < 0) return;
   int4 p = spos[s];
-  int rs = uf_root(parent, s);  // cached root of s; refreshed after every hook
+  int linked = 0;
   for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
-    if ((int)t <= s) return true;  // every unordered pair once
+    if ((int)t == s) return true;
     int4 q = spos[t];
     int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
     uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-    if (d < lfof2 && sigma[t] > T_L0) {
-      int rt = uf_root(parent, (int)t);
-      if (rt != rs) {
-        uf_unite(parent, rs, rt);
-        rs = uf_root(parent, rs);
-      }
+    if (d >= lfof2 || parent[t] < 0) return true;
+    uf_unite(parent, s, (int)t);
+    return ++linked < 2;
+  });
+}
+
+// point every dense particle straight at its current root
+__global__ void k_fof_compress(int* __restrict__ parent, int n) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n && parent[s] >= 0) parent[s] = uf_root(parent, s);
+}
+
+// every link (d < lfof2 between dense particles), each unordered pair once;
+// after the sampling round most neighbours already point at our root
+__global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __restrict__ spos, int n,
+                                                  uint32_t lfof2, int* __restrict__ parent) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || parent[s] < 0) return;
+  int4 p = spos[s];
+  int rs = uf_root(parent, s);  // cached root of s; refreshed after every hook
+  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+    if ((int)t <= s) return true;
+    int4 q = spos[t];
+    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
+    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+    if (d >= lfof2) return true;
+    int pt = parent[t];
+    if (pt < 0 || pt == rs) return true;  // not dense, or already under our root
+    int rt = uf_root(parent, pt);
+    if (rt != rs) {
+      uf_unite(parent, rs, rt);
+      rs = uf_root(parent, rs);
     }
     return true;
   });
@@ -191,7 +268,7 @@ __global__ void k_fof_finish(int* __restrict__ parent, int n, const long long* _
                              unsigned long long* __restrict__ minid) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  if (sigma[s] <= T_L0) {
+  if (parent[s] < 0) {
     root[s] = -1;
     return;
   }
@@ -247,10 +324,8 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
                   unsigned long long* pairs, cudaStream_t st) {
   if (n <= 0) return CSO_OK;
-  if (pairs)
-    k_density<true><<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, pairs);
-  else
-    k_density<false><<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, nullptr);
+  k_density<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma);
+  if (pairs) k_count_pairs<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, pairs);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;
 }
@@ -258,8 +333,10 @@ int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int i
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
               const uint64_t* sid, int* parent, int* root, unsigned long long* minid, cudaStream_t st) {
   if (n <= 0) return CSO_OK;
-  k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
-  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, sigma, T_L0, lfof2, parent);
+  k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0);
+  k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent);
+  k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
+  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
   CSO_CUDA(cudaGetLastError());

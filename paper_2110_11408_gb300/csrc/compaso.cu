@@ -356,62 +356,81 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
   return r;
 }
 
-// Step 2's density criterion for member e of the segment: no particle of the
-// same group (label) within d < b2 comes before it in key order.  The block
-// scans the 27-cell stencil of e cooperatively and stops at the first beater.
-__device__ bool block_is_peak(const LevelArgs& a, uint32_t se, int glabel, int* beaten, StencilRun* runs,
-                              unsigned* run_off, int* nrun) {
-  const int tid = threadIdx.x;
+// Step 2's density criterion for cell-sorted particle se of group glabel: no
+// particle of the same group within d < b2 comes before it in key order
+// (Sigma desc, id asc).  One warp scans the 27-cell stencil, its own cell row
+// first (where a denser neighbour usually sits), and stops at the first beater.
+__device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
+  const int lane = threadIdx.x & 31;
   const int4 p = a.spos[se];
   const long long sp = a.ssig[se];
   const uint64_t idp = a.sid[se];
-  if (tid == 0) {
-    int r = stencil_runs(a.grid, p.x, p.y, p.z, runs);
-    unsigned acc = 0;
-    for (int i = 0; i < r; ++i) {
-      run_off[i] = acc;
-      acc += runs[i].hi - runs[i].lo;
+  const int nc = a.grid.nc;
+  const int cx = cell_coord(p.x, nc), cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc);
+  // lane r < 9 looks up row r = (dz + 1) * 3 + (dy + 1): one run, or two where the row wraps in x
+  uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+  int qx1 = p.x, qy = p.y, qz = p.z;
+  if (lane < 9) {
+    int zz = cz + lane / 3 - 1, yy = cy + lane % 3 - 1;
+    if (zz < 0) { zz += nc; qz += CSO_BOX; } else if (zz >= nc) { zz -= nc; qz -= CSO_BOX; }
+    if (yy < 0) { yy += nc; qy += CSO_BOX; } else if (yy >= nc) { yy -= nc; qy -= CSO_BOX; }
+    const uint32_t* row = a.grid.start + ((size_t)zz * nc + yy) * nc;
+    if (cx >= 1 && cx + 1 < nc) {
+      lo0 = row[cx - 1];
+      hi0 = row[cx + 2];
+    } else if (cx == 0) {
+      lo0 = row[0];
+      hi0 = row[2];
+      lo1 = row[nc - 1];
+      hi1 = row[nc];
+      qx1 = p.x + CSO_BOX;
+    } else {
+      lo0 = row[nc - 2];
+      hi0 = row[nc];
+      lo1 = row[0];
+      hi1 = row[1];
+      qx1 = p.x - CSO_BOX;
     }
-    run_off[r] = acc;
-    *nrun = r;
-    *beaten = 0;
   }
-  __syncthreads();
-  const int r = *nrun;
-  const unsigned total = run_off[r];
-  for (unsigned f0 = 0; f0 < total; f0 += blockDim.x) {
-    unsigned f = f0 + tid;
-    if (f < total) {
-      int k = 0;
-      while (run_off[k + 1] <= f) ++k;
-      const StencilRun R = runs[k];
-      uint32_t t = R.lo + (f - run_off[k]);
-      if (t != se) {
-        int4 q = a.spos[t];
-        int dx = R.qx - q.x, dy = R.qy - q.y, dz = R.qz - q.z;
-        uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-        if (d < a.b2 && a.slab[t] == glabel) {
-          long long st = a.ssig[t];
-          if (st > sp || (st == sp && a.sid[t] < idp)) *beaten = 1;
+  for (int o = 0; o < 9; ++o) {
+    const int r = o == 0 ? 4 : (o <= 4 ? o - 1 : o);  // own row first
+    const uint32_t l0 = __shfl_sync(0xffffffffu, lo0, r), h0 = __shfl_sync(0xffffffffu, hi0, r);
+    const uint32_t l1 = __shfl_sync(0xffffffffu, lo1, r), h1 = __shfl_sync(0xffffffffu, hi1, r);
+    const int x1 = __shfl_sync(0xffffffffu, qx1, r), y = __shfl_sync(0xffffffffu, qy, r);
+    const int z = __shfl_sync(0xffffffffu, qz, r);
+    const uint32_t n0 = h0 - l0, tot = n0 + (h1 - l1);
+    for (uint32_t f0 = 0; f0 < tot; f0 += 32) {
+      const uint32_t f = f0 + lane;
+      bool beat = false;
+      if (f < tot) {
+        const uint32_t t = f < n0 ? l0 + f : l1 + (f - n0);
+        const int qx = f < n0 ? p.x : x1;
+        if (t != se) {
+          const int4 q = a.spos[t];
+          const int dx = qx - q.x, dy = y - q.y, dz = z - q.z;
+          const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+          if (d < a.b2 && a.slab[t] == glabel) {
+            const long long st = a.ssig[t];
+            beat = st > sp || (st == sp && a.sid[t] < idp);
+          }
         }
       }
+      if (__any_sync(0xffffffffu, beat)) return false;
     }
-    if (__syncthreads_or(*beaten)) break;
   }
-  bool peak = *beaten == 0;
-  __syncthreads();
-  return peak;
+  return true;
 }
 
 __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
+  constexpr int NW = LV_THREADS / 32;
   __shared__ SelShared S;
-  __shared__ StencilRun runs[18];
-  __shared__ unsigned run_off[19];
-  __shared__ int sP, sE, sNrun, sBeaten;
+  __shared__ int sP, sM;
+  __shared__ int list[LV_THREADS];
+  __shared__ int peak_of[NW];
   const int seg = blockIdx.x;
   const unsigned base = a.seg_off[seg];
   const int n = (int)(a.seg_off[seg + 1] - base);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4* epos = a.epos + base;
   const long long* esig = a.esig + base;
   const uint32_t* egs = a.egs + base;
@@ -439,60 +458,59 @@ __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
   const int glabel = a.slab[egs[0]];  // every member carries the group's label
   const long long anum2 = (long long)a.alpha_num * a.alpha_num, aden2 = (long long)a.alpha_den * a.alpha_den;
   int nn = 0;
-  int c = 0;
-  while (c < P) {
-    // step 2: the next eligible candidate in key order
-    if (tid == 0) sE = P;
+  for (int c0 = 0; c0 < P; c0 += LV_THREADS) {
+    // the eligible candidates of this chunk, in key order
+    const int j = c0 + tid;
+    const unsigned f = (j < P && !einel[j]) ? 1u : 0u;
+    unsigned excl;
+    const unsigned m = block_scan(f, excl, S.sw);
+    if (f) list[excl] = j;
     __syncthreads();
-    for (int c0 = c; c0 < P; c0 += 4 * LV_THREADS) {
-      int first = P;
-      for (int q = 0; q < 4; ++q) {
-        int j = c0 + tid * 4 + q;
-        if (j < P && !einel[j]) {
-          first = j;
-          break;
+    for (int g0 = 0; g0 < (int)m; g0 += NW) {
+      // step 2 for up to NW of them at once, one warp each (peak-ness never changes)
+      const int k = g0 + warp;
+      if (k < (int)m) {
+        const int e = list[k];
+        const bool ok = !einel[e] && warp_is_peak(a, egs[e], glabel);
+        if (lane == 0) peak_of[warp] = ok;
+      }
+      __syncthreads();
+      const int kmax = min(NW, (int)m - g0);
+      for (int kk = 0; kk < kmax; ++kk) {
+        const int e = list[g0 + kk];
+        // eligibility may have been lost to a nucleus found earlier in this walk
+        if (!peak_of[kk] || einel[e]) continue;
+        const int4 pc = epos[e];
+        const long long R2 = r_search(epos, ed, n, pc, a.pc, S, a.small_n, a.cap, a.nb);
+        // steps 1 and 3
+        for (int jj = tid; jj < n; jj += blockDim.x) {
+          long long d = ed[jj];
+          if (d >= R2) continue;
+          int s = eslot[jj];
+          bool take;
+          if (s < 0) {
+            take = true;
+          } else {
+            long long R2old = a.nuc_R2[base + s];
+            __int128 lhs = (__int128)R2 * edold[jj] * a.roche_den;
+            __int128 rhs = (__int128)a.roche_num * R2old * d;
+            take = lhs >= rhs;
+          }
+          if (take) {
+            eslot[jj] = nn;
+            edold[jj] = d;
+          }
+          if ((__int128)aden2 * d < (__int128)anum2 * R2) einel[jj] = 1;
         }
-      }
-      if (__syncthreads_or(first < P)) {
-        if (first < P) atomicMin(&sE, first);
+        if (tid == 0) {
+          a.nuc_member[base + nn] = (uint32_t)e;
+          a.nuc_R2[base + nn] = R2;
+        }
+        ++nn;
         __syncthreads();
-        break;
       }
+      __syncthreads();
     }
-    const int e = sE;
-    __syncthreads();
-    if (e >= P) break;
-    c = e + 1;
-    // ... which must also be denser than every group member within b
-    if (!block_is_peak(a, egs[e], glabel, &sBeaten, runs, run_off, &sNrun)) continue;
-    const int4 pc = epos[e];
-    const long long R2 = r_search(epos, ed, n, pc, a.pc, S, a.small_n, a.cap, a.nb);
-    // steps 1 and 3
-    for (int j = tid; j < n; j += blockDim.x) {
-      long long d = ed[j];
-      if (d >= R2) continue;
-      int s = eslot[j];
-      bool take;
-      if (s < 0) {
-        take = true;
-      } else {
-        long long R2old = a.nuc_R2[base + s];
-        __int128 lhs = (__int128)R2 * edold[j] * a.roche_den;
-        __int128 rhs = (__int128)a.roche_num * R2old * d;
-        take = lhs >= rhs;
-      }
-      if (take) {
-        eslot[j] = nn;
-        edold[j] = d;
-      }
-      if ((__int128)aden2 * d < (__int128)anum2 * R2) einel[j] = 1;
-    }
-    if (tid == 0) {
-      a.nuc_member[base + nn] = (uint32_t)e;
-      a.nuc_R2[base + nn] = R2;
-    }
-    ++nn;
-    __syncthreads();
   }
   if (tid == 0) {
     a.nnuc[seg] = (uint32_t)nn;
