@@ -103,6 +103,9 @@ extern "C" int cso_init(cso_ctx** out, int device, size_t budget, uint32_t flags
   c->budget = budget;
   c->flags = flags;
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, sizeof(long long) * 64);
   for (int i = 0; e == cudaSuccess && i <= CSO_MAX_STAGES; ++i) e = cudaEventCreate(&c->ev[i]);
   if (e != cudaSuccess) {
@@ -122,6 +125,10 @@ extern "C" void cso_free(cso_ctx* c) {
   if (c->pinned) cudaFreeHost(c->pinned);
   for (int i = 0; i <= CSO_MAX_STAGES; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->side) cudaStreamSynchronize(c->side);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -13,6 +13,7 @@
 //   pass B  tentative membership / competitive reassignment (Eq. 3) and
 //           eligibility marking.
 #include <float.h>
+#include <limits.h>
 
 #include "cells.cuh"
 #include "compaso.cuh"
@@ -124,16 +125,17 @@ __device__ __forceinline__ unsigned warp_incl(unsigned v) {
   return v;
 }
 
-// block exclusive scan (LV_THREADS threads), returns total
+// block exclusive scan (NT threads), returns total
+template <int NT>
 __device__ unsigned block_scan(unsigned v, unsigned& excl, unsigned* sw) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned inc = warp_incl(v);
   if (lane == 31) sw[w] = inc;
   __syncthreads();
   if (w == 0) {
-    unsigned s = lane < LV_THREADS / 32 ? sw[lane] : 0;
+    unsigned s = lane < NT / 32 ? sw[lane] : 0;
     unsigned si = warp_incl(s);
-    if (lane < LV_THREADS / 32) sw[lane] = si - s;
+    if (lane < NT / 32) sw[lane] = si - s;
     if (lane == 31) sw[32] = si;
   }
   __syncthreads();
@@ -196,6 +198,7 @@ __device__ __forceinline__ int pow2_at_least(int m) {
 }
 
 // R^2 of nucleus pc over the n members at epos[0..n); distances left in ed.
+template <int NT>
 __device__ long long r_search(const int4* __restrict__ epos, long long* __restrict__ ed, int n, int4 pc,
                               const PredConst& c, SelShared& S, const int small_n, const int cap, const int nb) {
   const int tid = threadIdx.x;
@@ -264,8 +267,8 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
     first_pass = false;
     // interior counts
     {
-      const int per = NB / LV_THREADS;
-      unsigned loc[NB / LV_THREADS];
+      constexpr int per = NB / NT;
+      unsigned loc[per];
       unsigned s = 0;
 #pragma unroll
       for (int q = 0; q < per; ++q) {
@@ -273,7 +276,7 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
         s += loc[q];
       }
       unsigned excl;
-      unsigned tot = block_scan(s, excl, S.sw);
+      unsigned tot = block_scan<NT>(s, excl, S.sw);
       unsigned run = excl;
 #pragma unroll
       for (int q = 0; q < per; ++q) {
@@ -421,13 +424,14 @@ __device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
   return true;
 }
 
-__global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
-  constexpr int NW = LV_THREADS / 32;
+// One group (segment) of a level, processed by a block of NT threads.
+template <int NT>
+__device__ void level_block(const LevelArgs& a, const int seg) {
+  constexpr int NW = NT / 32;
   __shared__ SelShared S;
   __shared__ int sP, sM;
-  __shared__ int list[LV_THREADS];
+  __shared__ int list[NT];
   __shared__ int peak_of[NW];
-  const int seg = blockIdx.x;
   const unsigned base = a.seg_off[seg];
   const int n = (int)(a.seg_off[seg + 1] - base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -458,12 +462,12 @@ __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
   const int glabel = a.slab[egs[0]];  // every member carries the group's label
   const long long anum2 = (long long)a.alpha_num * a.alpha_num, aden2 = (long long)a.alpha_den * a.alpha_den;
   int nn = 0;
-  for (int c0 = 0; c0 < P; c0 += LV_THREADS) {
+  for (int c0 = 0; c0 < P; c0 += NT) {
     // the eligible candidates of this chunk, in key order
     const int j = c0 + tid;
     const unsigned f = (j < P && !einel[j]) ? 1u : 0u;
     unsigned excl;
-    const unsigned m = block_scan(f, excl, S.sw);
+    const unsigned m = block_scan<NT>(f, excl, S.sw);
     if (f) list[excl] = j;
     __syncthreads();
     for (int g0 = 0; g0 < (int)m; g0 += NW) {
@@ -481,7 +485,7 @@ __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
         // eligibility may have been lost to a nucleus found earlier in this walk
         if (!peak_of[kk] || einel[e]) continue;
         const int4 pc = epos[e];
-        const long long R2 = r_search(epos, ed, n, pc, a.pc, S, a.small_n, a.cap, a.nb);
+        const long long R2 = r_search<NT>(epos, ed, n, pc, a.pc, S, a.small_n, a.cap, a.nb);
         // steps 1 and 3
         for (int jj = tid; jj < n; jj += blockDim.x) {
           long long d = ed[jj];
@@ -518,6 +522,141 @@ __global__ void __launch_bounds__(LV_THREADS) k_level(LevelArgs a) {
   }
 }
 
+template <int NT>
+__global__ void __launch_bounds__(NT) k_level(LevelArgs a, const uint32_t* __restrict__ segs) {
+  level_block<NT>(a, segs ? (int)segs[blockIdx.x] : (int)blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// One small group (n <= 64 members) per warp.  Members live in registers
+// (lane l holds members l and l + 32).  The enclosed count n(<d_i) of every
+// member is counted directly over all members (n^2 compares), so R^2 =
+// min{d_i : pred(n(<d_i), d_i)} needs no sort.
+// ---------------------------------------------------------------------------
+constexpr long long D_INF = LLONG_MAX;
+
+__device__ __forceinline__ long long warp_min_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t < v ? t : v;
+  }
+  return v;
+}
+
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  return v;
+}
+
+__device__ void level_warp(const LevelArgs& a, const int seg) {
+  const int lane = threadIdx.x & 31;
+  const unsigned base = a.seg_off[seg];
+  const int n = (int)(a.seg_off[seg + 1] - base);
+  const bool v0 = lane < n, v1 = lane + 32 < n;
+  const int4 p0 = v0 ? a.epos[base + lane] : make_int4(0, 0, 0, 0);
+  const int4 p1 = v1 ? a.epos[base + lane + 32] : make_int4(0, 0, 0, 0);
+  const long long s0 = v0 ? a.esig[base + lane] : LLONG_MIN;
+  const long long s1 = v1 ? a.esig[base + lane + 32] : LLONG_MIN;
+  const uint32_t g0 = v0 ? a.egs[base + lane] : 0, g1 = v1 ? a.egs[base + lane + 32] : 0;
+  int slot0 = -1, slot1 = -1;
+  bool in0 = false, in1 = false;
+  long long do0 = 0, do1 = 0;
+  // step 4: the members above the stop level form a prefix in key order
+  const int P = __popc(__ballot_sync(0xffffffffu, s0 > a.T_min)) + __popc(__ballot_sync(0xffffffffu, s1 > a.T_min));
+  const int glabel = a.slab[__shfl_sync(0xffffffffu, g0, 0)];
+  const long long anum2 = (long long)a.alpha_num * a.alpha_num, aden2 = (long long)a.alpha_den * a.alpha_den;
+  int nn = 0;
+  for (int c = 0; c < P; ++c) {
+    const int src = c & 31;
+    const bool hi = c >= 32;
+    const bool inel = __shfl_sync(0xffffffffu, hi ? in1 : in0, src);
+    if (inel) continue;
+    const uint32_t se = __shfl_sync(0xffffffffu, hi ? g1 : g0, src);
+    if (!warp_is_peak(a, se, glabel)) continue;
+    int4 pc;
+    pc.x = __shfl_sync(0xffffffffu, hi ? p1.x : p0.x, src);
+    pc.y = __shfl_sync(0xffffffffu, hi ? p1.y : p0.y, src);
+    pc.z = __shfl_sync(0xffffffffu, hi ? p1.z : p0.z, src);
+    const long long d0 = v0 ? dist2(pc, p0) : D_INF, d1 = v1 ? dist2(pc, p1) : D_INF;
+    // strictly enclosed counts
+    unsigned k0 = 0, k1 = 0;
+    for (int j = 0; j < n; ++j) {
+      const long long dj = __shfl_sync(0xffffffffu, j >= 32 ? d1 : d0, j & 31);
+      k0 += dj < d0;
+      k1 += dj < d1;
+    }
+    const bool ok0 = v0 && pred(k0, (unsigned long long)d0, a.pc);
+    const bool ok1 = v1 && pred(k1, (unsigned long long)d1, a.pc);
+    long long R2 = warp_min_ll(min(ok0 ? d0 : D_INF, ok1 ? d1 : D_INF));
+    if (R2 == D_INF) {
+      const long long dmax = warp_max_ll(max(v0 ? d0 : 0ll, v1 ? d1 : 0ll));
+      long long r = 0;
+      if (lane == 0) r = exhaust_radius((unsigned long long)n, dmax, a.pc);
+      R2 = __shfl_sync(0xffffffffu, r, 0);
+    }
+    // steps 1 and 3 on the two members of this lane
+    if (v0 && d0 < R2) {
+      bool take = slot0 < 0;
+      if (!take) {
+        const long long R2old = a.nuc_R2[base + slot0];
+        take = (__int128)R2 * do0 * a.roche_den >= (__int128)a.roche_num * R2old * d0;
+      }
+      if (take) {
+        slot0 = nn;
+        do0 = d0;
+      }
+      if ((__int128)aden2 * d0 < (__int128)anum2 * R2) in0 = true;
+    }
+    if (v1 && d1 < R2) {
+      bool take = slot1 < 0;
+      if (!take) {
+        const long long R2old = a.nuc_R2[base + slot1];
+        take = (__int128)R2 * do1 * a.roche_den >= (__int128)a.roche_num * R2old * d1;
+      }
+      if (take) {
+        slot1 = nn;
+        do1 = d1;
+      }
+      if ((__int128)aden2 * d1 < (__int128)anum2 * R2) in1 = true;
+    }
+    if (lane == 0) {
+      a.nuc_member[base + nn] = (uint32_t)c;
+      a.nuc_R2[base + nn] = R2;
+    }
+    __syncwarp();
+    ++nn;
+  }
+  if (v0) a.eslot[base + lane] = slot0;
+  if (v1) a.eslot[base + lane + 32] = slot1;
+  if (lane == 0) {
+    a.nnuc[seg] = (uint32_t)nn;
+    if (a.work && nn) atomicAdd(a.work, (unsigned long long)nn * (unsigned long long)n);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_level_warp(LevelArgs a, const uint32_t* __restrict__ segs, int count) {
+  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (w >= count) return;  // whole warps exit together
+  level_warp(a, (int)segs[w]);
+}
+
+// segment sizes as descending sort keys, and the size-bin counts
+__global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int giant, int small,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ val, unsigned* __restrict__ counts) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nseg) return;
+  const uint32_t sz = seg_off[g + 1] - seg_off[g];
+  key[g] = 0xffffffffu - sz;
+  val[g] = (uint32_t)g;
+  if (sz > (uint32_t)giant) atomicAdd(&counts[0], 1u);
+  else if (sz <= (uint32_t)small) atomicAdd(&counts[2], 1u);
+}
+
 // global halo index of every member (or -1) and per-halo nucleus records
 __global__ void k_level_halo(const uint32_t* __restrict__ seg_off, const uint32_t* __restrict__ nnuc,
                              const uint32_t* __restrict__ hbase, const int* __restrict__ eslot,
@@ -543,8 +682,46 @@ __global__ void k_level_halo(const uint32_t* __restrict__ seg_off, const uint32_
 
 int level_run(const LevelArgs& a, cudaStream_t st) {
   if (a.nseg <= 0) return CSO_OK;
-  k_level<<<CL(a.nseg), LV_THREADS, 0, st>>>(a);
+  k_level<256><<<CL(a.nseg), 256, 0, st>>>(a, nullptr);
   CSO_CUDA(cudaGetLastError());
+  return CSO_OK;
+}
+
+int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws, cudaStream_t st,
+                      cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, unsigned* host_counts) {
+  if (a.nseg <= 0) return CSO_OK;
+  size_t mark = ws.off;
+  uint32_t* key = ws.get<uint32_t>(a.nseg);
+  uint32_t* val = ws.get<uint32_t>(a.nseg);
+  uint32_t* key2 = ws.get<uint32_t>(a.nseg);
+  uint32_t* val2 = ws.get<uint32_t>(a.nseg);
+  unsigned* counts = ws.get<unsigned>(4);
+  if (!key || !val || !key2 || !val2 || !counts) {
+    cso_set_error("workspace exhausted in the batched schedule");
+    return CSO_ERR_BUDGET;
+  }
+  CSO_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned), st));
+  k_seg_sizes<<<CL(cdiv(a.nseg, 256)), 256, 0, st>>>(a.seg_off, a.nseg, sc.giant, sc.small, key, val, counts);
+  // largest groups first: giants start at once, the rest fill in behind them
+  uint32_t *pk = key, *pv = val;
+  CSO_TRY(radix_sort_32(&pk, &pv, key2, val2, a.nseg, 32, ws, st));
+  CSO_CUDA(cudaMemcpyAsync(host_counts, counts, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CSO_CUDA(cudaStreamSynchronize(st));
+  const int ng = (int)host_counts[0], ns = (int)host_counts[2], nm = a.nseg - ng - ns;
+  if (ng > 0) {
+    CSO_CUDA(cudaEventRecord(fork, st));
+    CSO_CUDA(cudaStreamWaitEvent(side, fork, 0));
+    k_level<1024><<<CL(ng), 1024, 0, side>>>(a, pv);
+    CSO_CUDA(cudaGetLastError());
+  }
+  if (nm > 0) k_level<256><<<CL(nm), 256, 0, st>>>(a, pv + ng);
+  if (ns > 0) k_level_warp<<<CL(cdiv(ns, 8)), 256, 0, st>>>(a, pv + ng + nm, ns);
+  CSO_CUDA(cudaGetLastError());
+  if (ng > 0) {
+    CSO_CUDA(cudaEventRecord(join, side));
+    CSO_CUDA(cudaStreamWaitEvent(st, join, 0));
+  }
+  ws.off = mark;
   return CSO_OK;
 }
 

@@ -491,7 +491,11 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   L1.small_n = stress ? 8 : 2048;
   L1.cap = stress ? 8 : 2048;
   L1.nb = stress ? 16 : 1024;
-  CSO_TRY(level_run(L1, st));
+  const bool batched = (c->flags & CSO_FLAG_BATCHED) != 0;
+  LevelSchedule sched;
+  unsigned* hcounts = (unsigned*)(c->pinned + 32);
+  if (batched) CSO_TRY(level_run_batched(L1, sched, ws, st, c->side, c->fork, c->join, hcounts));
+  else CSO_TRY(level_run(L1, st));
 
   // ---- prep2: L1 haloes, their members in key order, peaks within L1 ----
   S.mark("prep2");
@@ -553,7 +557,9 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   L2.nuc_R2 = nucR22;
   L2.nnuc = nnuc2;
   L2.work = &meta->work2;
-  CSO_TRY(level_run(L2, st));  // edold / einel / ed are reused (na <= nd)
+  // edold / einel / ed are reused (na <= nd)
+  if (batched) CSO_TRY(level_run_batched(L2, sched, ws, st, c->side, c->fork, c->join, hcounts));
+  else CSO_TRY(level_run(L2, st));
 
   // ---- output ----
   S.mark("output");

@@ -20,6 +20,8 @@ struct ServedReq {
 struct cso_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;  // second stream of the batched schedule (giant groups)
+  cudaEvent_t fork = nullptr, join = nullptr;
   size_t budget = 0;
   uint32_t flags = 0;
   Workspace ws;
