@@ -26,47 +26,6 @@ __device__ __forceinline__ int wrap_cell(int c, int nc, int& shift) {
 
 __device__ __forceinline__ int cell_of(int x, int nc) { return cell_coord(x, nc); }
 
-// Visit every sorted index t whose cell is in the 27-stencil of the query;
-// f(t, xq, yq, zq) receives the shifted query coordinates.  f returns false to stop.
-template <class F>
-__device__ __forceinline__ void for_stencil(const CellGrid& g, int x, int y, int z, F f) {
-  const int nc = g.nc;
-  const int cx = cell_of(x, nc), cy = cell_of(y, nc), cz = cell_of(z, nc);
-  for (int dz = -1; dz <= 1; ++dz) {
-    int sz;
-    int zz = wrap_cell(cz + dz, nc, sz);
-    for (int dy = -1; dy <= 1; ++dy) {
-      int sy;
-      int yy = wrap_cell(cy + dy, nc, sy);
-      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
-      const int yq = y + sy, zq = z + sz;
-      // the three x cells: one contiguous run unless the row wraps
-      uint32_t lo0, hi0, lo1 = 0, hi1 = 0;
-      int sx1 = 0;
-      if (cx >= 1 && cx + 1 < nc) {
-        lo0 = row[cx - 1];
-        hi0 = row[cx + 2];
-      } else if (cx == 0) {
-        lo0 = row[0];
-        hi0 = row[2];
-        lo1 = row[nc - 1];
-        hi1 = row[nc];
-        sx1 = CSO_BOX;
-      } else {  // cx == nc - 1
-        lo0 = row[nc - 2];
-        hi0 = row[nc];
-        lo1 = row[0];
-        hi1 = row[1];
-        sx1 = -CSO_BOX;
-      }
-      for (uint32_t t = lo0; t < hi0; ++t)
-        if (!f(t, x, yq, zq)) return;
-      for (uint32_t t = lo1; t < hi1; ++t)
-        if (!f(t, x + sx1, yq, zq)) return;
-    }
-  }
-}
-
 __global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, int nc, uint32_t* __restrict__ key,
                              uint32_t* __restrict__ rank, uint32_t* __restrict__ count, int* __restrict__ bad) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,55 +57,17 @@ __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_
   return b2 - (d < b2 ? d : b2);  // b2 - d inside the kernel support, else 0
 }
 
-__device__ __forceinline__ unsigned long long sum_run(const int4* __restrict__ spos, uint32_t t, uint32_t e, int xq,
-                                                      int yq, int zq, uint32_t b2) {
-  unsigned long long acc = 0;
-  // four independent loads in flight; four terms < 2^28 each fit a uint32
-  for (; t + 4 <= e; t += 4) {
-    const int4 q0 = spos[t], q1 = spos[t + 1], q2 = spos[t + 2], q3 = spos[t + 3];
-    acc += kern(q0, xq, yq, zq, b2) + kern(q1, xq, yq, zq, b2) + kern(q2, xq, yq, zq, b2) +
-           kern(q3, xq, yq, zq, b2);
-  }
-  for (; t < e; ++t) acc += kern(spos[t], xq, yq, zq, b2);
-  return acc;
-}
-
-// Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2).
-// Away from the x faces of the box the 9 rows of the stencil are looked up
-// first, so the 18 table loads are in flight together; particles in the
-// first or last x cell (a row that wraps) take the general stencil walk.
+// Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2)
 __global__ void __launch_bounds__(256) k_density(CellGrid g, const int4* __restrict__ spos, int n, uint32_t b2,
                                                  int include_self, long long* __restrict__ sigma) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int4 p = spos[s];
-  const int nc = g.nc;
-  const int cx = cell_of(p.x, nc), cy = cell_of(p.y, nc), cz = cell_of(p.z, nc);
   unsigned long long acc = 0;
-  if (cx >= 1 && cx + 1 < nc) {
-    uint32_t lo[9], hi[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      int sz, sy;
-      const int zz = wrap_cell(cz + r / 3 - 1, nc, sz);
-      const int yy = wrap_cell(cy + r % 3 - 1, nc, sy);
-      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
-      lo[r] = row[cx - 1];
-      hi[r] = row[cx + 2];
-    }
-#pragma unroll
-    for (int r = 0; r < 9; ++r) {
-      int sz, sy;
-      wrap_cell(cz + r / 3 - 1, nc, sz);
-      wrap_cell(cy + r % 3 - 1, nc, sy);
-      acc += sum_run(spos, lo[r], hi[r], p.x, p.y + sy, p.z + sz, b2);
-    }
-  } else {
-    for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
-      acc += kern(spos[t], xq, yq, zq, b2);
-      return true;
-    });
-  }
+  for_stencil_r(g, p.x, p.y, p.z, b2, [&](uint32_t t, int xq, int yq, int zq) {
+    acc += kern(spos[t], xq, yq, zq, b2);
+    return true;
+  });
   // the particle met itself once at d = 0
   if (!include_self) acc -= b2;
   sigma[s] = (long long)acc;
@@ -160,7 +81,7 @@ __global__ void __launch_bounds__(256) k_count_pairs(CellGrid g, const int4* __r
   unsigned cnt = 0;
   if (s < n) {
     const int4 p = spos[s];
-    for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+    for_stencil_r(g, p.x, p.y, p.z, b2, [&](uint32_t t, int xq, int yq, int zq) {
       cnt += kern(spos[t], xq, yq, zq, b2) != 0;
       return true;
     });
@@ -212,23 +133,25 @@ __global__ void k_fof_init(int* __restrict__ parent, int n, const long long* __r
 }
 
 // Sampling round (the idea of Afforest, Sutton et al. 2018): hook every dense
-// particle to its first two linked neighbours.  In dense regions this already
-// joins almost every particle to its final component.
+// particle to the first two linked neighbours in its own cell.  In dense
+// regions this already joins almost every particle to its final component.
 __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __restrict__ spos, int n,
                                                     uint32_t lfof2, int* __restrict__ parent) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || parent[s] < 0) return;
-  int4 p = spos[s];
+  const int4 p = spos[s];
+  const int nc = g.nc;
+  const size_t cell = ((size_t)cell_of(p.z, nc) * nc + cell_of(p.y, nc)) * nc + cell_of(p.x, nc);
   int linked = 0;
-  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
-    if ((int)t == s) return true;
-    int4 q = spos[t];
-    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
-    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-    if (d >= lfof2 || parent[t] < 0) return true;
+  for (uint32_t t = g.start[cell], e = g.start[cell + 1]; t < e && linked < 2; ++t) {
+    if ((int)t == s) continue;
+    const int4 q = spos[t];
+    const int dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+    const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+    if (d >= lfof2 || parent[t] < 0) continue;
     uf_unite(parent, s, (int)t);
-    return ++linked < 2;
-  });
+    ++linked;
+  }
 }
 
 // point every dense particle straight at its current root
@@ -245,7 +168,7 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
   if (s >= n || parent[s] < 0) return;
   int4 p = spos[s];
   int rs = uf_root(parent, s);  // cached root of s; refreshed after every hook
-  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) {
+  for_stencil_r(g, p.x, p.y, p.z, lfof2, [&](uint32_t t, int xq, int yq, int zq) {
     if ((int)t <= s) return true;
     int4 q = spos[t];
     int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;

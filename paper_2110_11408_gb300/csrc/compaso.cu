@@ -370,29 +370,33 @@ __device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
   const uint64_t idp = a.sid[se];
   const int nc = a.grid.nc;
   const int cx = cell_coord(p.x, nc), cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc);
-  // lane r < 9 looks up row r = (dz + 1) * 3 + (dy + 1): one run, or two where the row wraps in x
+  // lane r < 9 looks up row r = (dz + 1) * 3 + (dy + 1), dropping the rows and
+  // end cells that cannot reach within b (one run, plus one where the row wraps)
   uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
   int qx1 = p.x, qy = p.y, qz = p.z;
   if (lane < 9) {
-    int zz = cz + lane / 3 - 1, yy = cy + lane % 3 - 1;
-    if (zz < 0) { zz += nc; qz += CSO_BOX; } else if (zz >= nc) { zz -= nc; qz -= CSO_BOX; }
-    if (yy < 0) { yy += nc; qy += CSO_BOX; } else if (yy >= nc) { yy -= nc; qy -= CSO_BOX; }
-    const uint32_t* row = a.grid.start + ((size_t)zz * nc + yy) * nc;
-    if (cx >= 1 && cx + 1 < nc) {
-      lo0 = row[cx - 1];
-      hi0 = row[cx + 2];
-    } else if (cx == 0) {
-      lo0 = row[0];
-      hi0 = row[2];
-      lo1 = row[nc - 1];
-      hi1 = row[nc];
-      qx1 = p.x + CSO_BOX;
-    } else {
-      lo0 = row[nc - 2];
-      hi0 = row[nc];
-      lo1 = row[0];
-      hi1 = row[1];
-      qx1 = p.x - CSO_BOX;
+    const int dz = lane / 3 - 1, dy = lane % 3 - 1;
+    const long long zl = p.z - cell_lo(cz, nc) + 1, zr = cell_lo(cz + 1, nc) - p.z;
+    const long long yl = p.y - cell_lo(cy, nc) + 1, yr = cell_lo(cy + 1, nc) - p.y;
+    const long long xl = p.x - cell_lo(cx, nc) + 1, xr = cell_lo(cx + 1, nc) - p.x;
+    const long long m = (dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0)) + (dy < 0 ? yl * yl : (dy > 0 ? yr * yr : 0));
+    if (m < (long long)a.b2) {
+      int zz = cz + dz, yy = cy + dy;
+      if (zz < 0) { zz += nc; qz += CSO_BOX; } else if (zz >= nc) { zz -= nc; qz -= CSO_BOX; }
+      if (yy < 0) { yy += nc; qy += CSO_BOX; } else if (yy >= nc) { yy -= nc; qy -= CSO_BOX; }
+      const uint32_t* row = a.grid.start + ((size_t)zz * nc + yy) * nc;
+      const bool left = m + xl * xl < (long long)a.b2, right = m + xr * xr < (long long)a.b2;
+      int ca = cx, cb = cx;
+      if (left) {
+        if (cx > 0) ca = cx - 1;
+        else { lo1 = row[nc - 1]; hi1 = row[nc]; qx1 = p.x + CSO_BOX; }
+      }
+      if (right) {
+        if (cx + 1 < nc) cb = cx + 1;
+        else { lo1 = row[0]; hi1 = row[1]; qx1 = p.x - CSO_BOX; }
+      }
+      lo0 = row[ca];
+      hi0 = row[cb + 1];
     }
   }
   for (int o = 0; o < 9; ++o) {
