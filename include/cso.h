@@ -184,6 +184,29 @@ int cso_last_stats(cso_ctx* ctx, int64_t* out, int cap);
 /* One-line description of the last error of this thread. */
 const char* cso_last_error(void);
 
+/* --- kernel density without device allocation ---------------------------
+ *
+ * The paper has no counterpart of this entry point: it exists for callers
+ * that cannot allocate device memory where they need the densities (an
+ * N-body code that has given all device memory to its own pool, or a
+ * time-step loop in which a cudaMalloc would synchronise the device).
+ *
+ * Computes Sigma_i (as in cso_output.sigma) for n particles.  pos (int32
+ * [n][3]) and sigma (int64 [n], input order) are DEVICE pointers owned by
+ * the caller; stream is a cudaStream_t (NULL = legacy default stream); the
+ * call returns after the work on that stream has completed.  The scratch
+ * lives in one fixed 64 MiB array in device memory that every GPU which
+ * loads this library holds until the process exits; nothing is allocated or
+ * freed.  Limits: n <= CSO_STATIC_MAX_N and at most CSO_STATIC_MAX_CELLS
+ * cells (boxes of up to 64 l_mean per side at the default b); larger requests
+ * return CSO_ERR_ARG.  The first call on a device looks up the array's
+ * device address, so make it before any stream capture.  All calls share
+ * the one array: calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialised by the caller. */
+#define CSO_STATIC_MAX_N (1 << 20)
+#define CSO_STATIC_MAX_CELLS (1 << 22)
+int cso_density_static(const int32_t* pos, int64_t n, const cso_params* p, int64_t* sigma, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
