@@ -154,7 +154,7 @@ extern "C" int cso_last_stats(cso_ctx* c, int64_t* out, int cap) {
 
 // workspace large enough for n particles and ncell cells
 int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io) {
-  size_t need = (size_t)n * CSO_BYTES_PER_PARTICLE + (size_t)(ncell + 1) * 4 + ((size_t)64 << 20);
+  size_t need = (size_t)n * CSO_BYTES_PER_PARTICLE + (size_t)(ncell + 1) * 8 + ((size_t)64 << 20);
   if (host_io) need += (size_t)n * (12 + 8 + 32) + (size_t)n / 2 * sizeof(cso_halo);
   if (c->budget && need > c->budget) {
     cso_set_error("request needs %zu bytes of workspace, budget is %zu", need, c->budget);

@@ -26,6 +26,47 @@ __device__ __forceinline__ int wrap_cell(int c, int nc, int& shift) {
 
 __device__ __forceinline__ int cell_of(int x, int nc) { return cell_coord(x, nc); }
 
+// Visit every cell-sorted index t in the 27-cell stencil of the query, row
+// by row (the three x-cells of a row are one contiguous run unless the row
+// wraps); f(t, xq, yq, zq) receives the query shifted by whole boxes so that
+// plain differences are minimum-image offsets.  No culling: lanes of a warp
+// in one cell walk the same runs, which keeps the warp converged.
+template <class F>
+__device__ __forceinline__ void for_stencil(const CellGrid& g, int x, int y, int z, F f) {
+  const int nc = g.nc;
+  const int cx = cell_of(x, nc), cy = cell_of(y, nc), cz = cell_of(z, nc);
+  for (int dz = -1; dz <= 1; ++dz) {
+    int sz;
+    const int zz = wrap_cell(cz + dz, nc, sz);
+    for (int dy = -1; dy <= 1; ++dy) {
+      int sy;
+      const int yy = wrap_cell(cy + dy, nc, sy);
+      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
+      const int yq = y + sy, zq = z + sz;
+      uint32_t lo0, hi0, lo1 = 0, hi1 = 0;
+      int sx1 = 0;
+      if (cx >= 1 && cx + 1 < nc) {
+        lo0 = row[cx - 1];
+        hi0 = row[cx + 2];
+      } else if (cx == 0) {
+        lo0 = row[0];
+        hi0 = row[2];
+        lo1 = row[nc - 1];
+        hi1 = row[nc];
+        sx1 = CSO_BOX;
+      } else {
+        lo0 = row[nc - 2];
+        hi0 = row[nc];
+        lo1 = row[0];
+        hi1 = row[1];
+        sx1 = -CSO_BOX;
+      }
+      for (uint32_t t = lo0; t < hi0; ++t) f(t, x, yq, zq);
+      for (uint32_t t = lo1; t < hi1; ++t) f(t, x + sx1, yq, zq);
+    }
+  }
+}
+
 __global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, int nc, uint32_t* __restrict__ key,
                              uint32_t* __restrict__ rank, uint32_t* __restrict__ count, int* __restrict__ bad) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,10 +105,7 @@ __global__ void __launch_bounds__(256) k_density(CellGrid g, const int4* __restr
   if (s >= n) return;
   const int4 p = spos[s];
   unsigned long long acc = 0;
-  for_stencil_r(g, p.x, p.y, p.z, b2, [&](uint32_t t, int xq, int yq, int zq) {
-    acc += kern(spos[t], xq, yq, zq, b2);
-    return true;
-  });
+  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) { acc += kern(spos[t], xq, yq, zq, b2); });
   // the particle met itself once at d = 0
   if (!include_self) acc -= b2;
   sigma[s] = (long long)acc;
@@ -81,10 +119,7 @@ __global__ void __launch_bounds__(256) k_count_pairs(CellGrid g, const int4* __r
   unsigned cnt = 0;
   if (s < n) {
     const int4 p = spos[s];
-    for_stencil_r(g, p.x, p.y, p.z, b2, [&](uint32_t t, int xq, int yq, int zq) {
-      cnt += kern(spos[t], xq, yq, zq, b2) != 0;
-      return true;
-    });
+    for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) { cnt += kern(spos[t], xq, yq, zq, b2) != 0; });
     cnt -= 1;  // the particle itself
   }
   unsigned tot = __reduce_add_sync(0xffffffffu, cnt);
@@ -133,8 +168,8 @@ __global__ void k_fof_init(int* __restrict__ parent, int n, const long long* __r
 }
 
 // Sampling round (the idea of Afforest, Sutton et al. 2018): hook every dense
-// particle to the first two linked neighbours in its own cell.  In dense
-// regions this already joins almost every particle to its final component.
+// particle to the first few linked neighbours in its own cell.  In dense
+// regions this joins almost every cell's dense particles into one tree.
 __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __restrict__ spos, int n,
                                                     uint32_t lfof2, int* __restrict__ parent) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,7 +178,7 @@ __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __re
   const int nc = g.nc;
   const size_t cell = ((size_t)cell_of(p.z, nc) * nc + cell_of(p.y, nc)) * nc + cell_of(p.x, nc);
   int linked = 0;
-  for (uint32_t t = g.start[cell], e = g.start[cell + 1]; t < e && linked < 2; ++t) {
+  for (uint32_t t = g.start[cell], e = g.start[cell + 1]; t < e && linked < 4; ++t) {
     if ((int)t == s) continue;
     const int4 q = spos[t];
     const int dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
@@ -160,29 +195,77 @@ __global__ void k_fof_compress(int* __restrict__ parent, int n) {
   if (s < n && parent[s] >= 0) parent[s] = uf_root(parent, s);
 }
 
-// every link (d < lfof2 between dense particles), each unordered pair once;
-// after the sampling round most neighbours already point at our root
+// cell_root[c]: the common root of the dense particles of cell c, CELL_MIXED
+// if they are in several trees, CELL_EMPTY if the cell has none.  Filled
+// after compression, when parent[] holds roots.
+constexpr int CELL_EMPTY = -2, CELL_MIXED = -1;
+
+__global__ void k_cell_root_init(int* __restrict__ cell_root, long long ncell) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ncell) cell_root[c] = CELL_EMPTY;
+}
+
+__global__ void k_cell_root(const int4* __restrict__ spos, int n, int nc, const int* __restrict__ parent,
+                            int* __restrict__ cell_root) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int r = parent[s];
+  if (r < 0) return;
+  const int4 p = spos[s];
+  const size_t c = ((size_t)cell_of(p.z, nc) * nc + cell_of(p.y, nc)) * nc + cell_of(p.x, nc);
+  int old = atomicCAS(&cell_root[c], CELL_EMPTY, r);
+  if (old != CELL_EMPTY && old != r && old != CELL_MIXED) atomicExch(&cell_root[c], CELL_MIXED);
+}
+
+// Every link (d < lfof2 between dense particles) that can still join two
+// trees.  A neighbour cell whose dense particles share one tree is skipped
+// when that tree is already ours, and left after its first link otherwise
+// (the link joins the whole cell); mixed cells are walked in full, each
+// unordered pair once.
 __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __restrict__ spos, int n,
-                                                  uint32_t lfof2, int* __restrict__ parent) {
+                                                  uint32_t lfof2, int* __restrict__ parent,
+                                                  const int* __restrict__ cell_root) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || parent[s] < 0) return;
-  int4 p = spos[s];
-  int rs = uf_root(parent, s);  // cached root of s; refreshed after every hook
-  for_stencil_r(g, p.x, p.y, p.z, lfof2, [&](uint32_t t, int xq, int yq, int zq) {
-    if ((int)t <= s) return true;
-    int4 q = spos[t];
-    int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
-    uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-    if (d >= lfof2) return true;
-    int pt = parent[t];
-    if (pt < 0 || pt == rs) return true;  // not dense, or already under our root
-    int rt = uf_root(parent, pt);
-    if (rt != rs) {
-      uf_unite(parent, rs, rt);
-      rs = uf_root(parent, rs);
+  const int4 p = spos[s];
+  const int nc = g.nc;
+  const int cx = cell_of(p.x, nc), cy = cell_of(p.y, nc), cz = cell_of(p.z, nc);
+  int rs = uf_root(parent, s);
+  for (int dz = -1; dz <= 1; ++dz) {
+    int sz;
+    const int zz = wrap_cell(cz + dz, nc, sz);
+    for (int dy = -1; dy <= 1; ++dy) {
+      int sy;
+      const int yy = wrap_cell(cy + dy, nc, sy);
+      for (int dx = -1; dx <= 1; ++dx) {
+        int sx;
+        const int xx = wrap_cell(cx + dx, nc, sx);
+        const size_t c = ((size_t)zz * nc + yy) * nc + xx;
+        const int cr = cell_root[c];
+        if (cr == CELL_EMPTY) continue;
+        const bool unified = cr >= 0;
+        if (unified && uf_root(parent, cr) == rs) continue;
+        const int xq = p.x + sx, yq = p.y + sy, zq = p.z + sz;
+        for (uint32_t t = g.start[c], e = g.start[c + 1]; t < e; ++t) {
+          if (!unified && (int)t <= s) continue;
+          const int4 q = spos[t];
+          const int ddx = xq - q.x, ddy = yq - q.y, ddz = zq - q.z;
+          const uint32_t d = (uint32_t)(ddx * ddx) + (uint32_t)(ddy * ddy) + (uint32_t)(ddz * ddz);
+          if (d >= lfof2) continue;
+          const int pt = parent[t];
+          if (pt < 0) continue;
+          if (pt != rs) {
+            const int rt = uf_root(parent, pt);
+            if (rt != rs) {
+              uf_unite(parent, rs, rt);
+              rs = uf_root(parent, rs);
+            }
+          }
+          if (unified) break;  // one link joins the whole cell to our tree
+        }
+      }
     }
-    return true;
-  });
+  }
 }
 
 // root of every dense particle (-1 otherwise); smallest id per root
@@ -254,12 +337,16 @@ int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int i
 }
 
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
-              const uint64_t* sid, int* parent, int* root, unsigned long long* minid, cudaStream_t st) {
+              const uint64_t* sid, int* parent, int* root, unsigned long long* minid, int* cell_root,
+              cudaStream_t st) {
   if (n <= 0) return CSO_OK;
+  const long long ncell = (long long)g.nc * g.nc * g.nc;
   k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0);
   k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent);
   k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
-  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent);
+  k_cell_root_init<<<CL(cdiv(ncell, 256)), 256, 0, st>>>(cell_root, ncell);
+  k_cell_root<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, n, g.nc, parent, cell_root);
+  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent, cell_root);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
   CSO_CUDA(cudaGetLastError());

@@ -102,4 +102,5 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
                   unsigned long long* pairs, cudaStream_t st);
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
-              const uint64_t* sid, int* parent, int* root, unsigned long long* minid, cudaStream_t st);
+              const uint64_t* sid, int* parent, int* root, unsigned long long* minid, int* cell_root,
+              cudaStream_t st);

@@ -391,7 +391,12 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   ALLOC(int, parent, n);
   ALLOC(int, root, n);
   ALLOC(unsigned long long, minid, n);
-  CSO_TRY(cells_fof(g, spos, N, sigma, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, st));
+  {
+    size_t mark = ws.off;
+    ALLOC(int, cell_root, ncell);  // per-cell tree summary, transient
+    CSO_TRY(cells_fof(g, spos, N, sigma, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, cell_root, st));
+    ws.off = mark;
+  }
 
   // ---- gather: dense particles by (group, Sigma desc, id asc) ----
   S.mark("gather");
