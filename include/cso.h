@@ -50,6 +50,8 @@ extern "C" {
 #define CSO_FLAG_GRAPH 4u   /* replay the batched CompaSO launch sequence as a CUDA graph */
 #define CSO_FLAG_COUNT_PAIRS 8u /* count kernel pairs with d < b2 (cso_last_stats[6]); slows the density pass */
 #define CSO_FLAG_SELECT_STRESS 16u /* testing: tiny radius-search tiles so every select branch runs; same results */
+/* served path: number of worker slots (concurrent requests), 1..15; 0 = 4 */
+#define CSO_FLAG_SLOTS(k) ((uint32_t)((k) & 0xf) << 8)
 
 /*
  * Parameters (Table 1 of the paper; Einstein-de Sitter thresholds of
@@ -151,15 +153,29 @@ int cso_params_derive(cso_params* p);
  * labels and catalogue.  Synchronous: returns after the outputs are written. */
 int cso_find_groups(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out);
 
-/* Served path: queue a box for asynchronous processing on the context's
- * stream pool and return a ticket.  The buffers behind `in` and `out` must
- * stay valid until cso_poll reports the ticket done. */
+/* Served path (continuous batching).  Queue a box and return a ticket at
+ * once: CSO_OK if it was admitted immediately, CSO_EAGAIN if it waits (the
+ * ticket is valid either way), CSO_ERR_BUDGET if it can never fit the
+ * context's device-memory budget.  Requests are admitted in submission order
+ * onto the context's worker slots (CSO_FLAG_SLOTS, each with its own
+ * streams and workspace) while a slot is free and the workspace of all
+ * running requests stays within the budget; admitted requests run
+ * concurrently and each gives exactly the outputs cso_find_groups gives it
+ * alone.  `in`, `out` and every buffer behind them must stay valid until
+ * cso_poll reports the ticket done. */
 int cso_submit(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out, uint64_t* ticket);
 
 /* Wait up to timeout_us (0 = just test, <0 = wait forever) for a ticket;
  * *done = 1 when its outputs are complete; returns the request's own status
- * once done. */
+ * once done (CSO_OK while still running).  CSO_ERR_STATE: unknown ticket. */
 int cso_poll(cso_ctx* ctx, uint64_t ticket, int32_t* done, int32_t timeout_us);
+
+/* Host steady-clock times (seconds, the cso_clock() scale) at which a done
+ * ticket was submitted, admitted and completed. */
+int cso_ticket_times(cso_ctx* ctx, uint64_t ticket, double* t_submit, double* t_start, double* t_done);
+
+/* The library's host steady clock, seconds. */
+double cso_clock(void);
 
 /* Release every resource of the context. */
 void cso_free(cso_ctx* ctx);

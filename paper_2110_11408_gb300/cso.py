@@ -35,6 +35,11 @@ FLAG_GRAPH = 4
 FLAG_COUNT_PAIRS = 8
 FLAG_SELECT_STRESS = 16
 
+
+def FLAG_SLOTS(k):
+    """served path: number of concurrent worker slots (1..15)"""
+    return (int(k) & 0xF) << 8
+
 STAT_NAMES = ["n", "dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows", "pairs_b", "l1_work",
               "l2_work", "workspace_bytes", "launches"]
 
@@ -115,6 +120,9 @@ def lib(build_if_missing=True):
         L.cso_stage_times.argtypes = [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_char_p), ctypes.c_int]
         L.cso_last_stats.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), ctypes.c_int]
         L.cso_last_error.restype = ctypes.c_char_p
+        L.cso_ticket_times.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double),
+                                       P(ctypes.c_double)]
+        L.cso_clock.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -232,6 +240,18 @@ def cso_poll(ctx, ticket, timeout_us=-1):
     return bool(done.value), rc
 
 
+def cso_ticket_times(ctx, ticket):
+    """(t_submit, t_start, t_done) of a finished ticket, host steady clock (s)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().cso_ticket_times(ctx, ctypes.c_uint64(ticket), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "cso_ticket_times")
+    return a.value, b.value, c.value
+
+
+def cso_clock():
+    return lib().cso_clock()
+
+
 def cso_stream(ctx):
     return lib().cso_stream(ctx)
 
@@ -291,6 +311,14 @@ class Context:
         b = Buffers(pos, ids, on_device, halo_cap=halo_cap)
         cso_find_groups(self.h, b, params)
         return b.result()
+
+    def submit(self, buffers, params):
+        """Served path: queue one request; keep `buffers` alive until done."""
+        return cso_submit(self.h, buffers, params)
+
+    def wait(self, ticket, timeout_us=-1):
+        done, rc = cso_poll(self.h, ticket, timeout_us)
+        return done, rc
 
     def stage_times(self):
         return cso_stage_times(self.h)

@@ -15,7 +15,7 @@
 // errors
 // ---------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
-long long g_cso_launches = 0;
+thread_local long long g_cso_launches = 0;
 
 void cso_set_error(const char* fmt, ...) {
   va_list ap;
@@ -102,6 +102,7 @@ extern "C" int cso_init(cso_ctx** out, int device, size_t budget, uint32_t flags
   c->device = device;
   c->budget = budget;
   c->flags = flags;
+  c->served_slots = (int)((flags >> 8) & 0xf);
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
@@ -119,6 +120,7 @@ extern "C" int cso_init(cso_ctx** out, int device, size_t budget, uint32_t flags
 
 extern "C" void cso_free(cso_ctx* c) {
   if (!c) return;
+  served_stop(c);
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->ws.base) cudaFree(c->ws.base);
@@ -153,9 +155,14 @@ extern "C" int cso_last_stats(cso_ctx* c, int64_t* out, int cap) {
 }
 
 // workspace large enough for n particles and ncell cells
-int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io) {
+size_t workspace_bytes(long long n, long long ncell, bool host_io) {
   size_t need = (size_t)n * CSO_BYTES_PER_PARTICLE + (size_t)(ncell + 1) * 8 + ((size_t)64 << 20);
-  if (host_io) need += (size_t)n * (12 + 8 + 32) + (size_t)n / 2 * sizeof(cso_halo);
+  if (host_io) need += (size_t)n * (12 + 8 + 32);
+  return need;
+}
+
+int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io) {
+  size_t need = workspace_bytes(n, ncell, host_io);
   if (c->budget && need > c->budget) {
     cso_set_error("request needs %zu bytes of workspace, budget is %zu", need, c->budget);
     return CSO_ERR_BUDGET;
@@ -178,7 +185,7 @@ int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io) {
 // ---------------------------------------------------------------------------
 // entry points
 // ---------------------------------------------------------------------------
-static int check_io(const cso_input* in, const cso_params* p, cso_output* out) {
+int check_io(const cso_input* in, const cso_params* p, cso_output* out) {
   if (!in || !p || !out || in->n < 0 || (in->n > 0 && (!in->pos || !in->ids))) {
     cso_set_error("null or negative argument");
     return CSO_ERR_ARG;
@@ -202,48 +209,4 @@ extern "C" int cso_find_groups(cso_ctx* c, const cso_input* in, const cso_params
   CSO_CUDA(cudaSetDevice(c->device));
   int rc = pipeline_run(c, in, &p, out);
   return rc;
-}
-
-// Served path.  Requests are queued and run in submission order on the
-// context's stream when cso_poll (or a later cso_submit) drives the queue.
-extern "C" int cso_submit(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out, uint64_t* ticket) {
-  if (!c || !ticket) return CSO_ERR_ARG;
-  CSO_TRY(check_io(in, p, out));
-  ServedReq r;
-  r.in = *in;
-  r.p = *p;
-  r.out = out;
-  r.ticket = ++c->next_ticket;
-  c->queue.push_back(r);
-  *ticket = r.ticket;
-  return CSO_EAGAIN;
-}
-
-extern "C" int cso_poll(cso_ctx* c, uint64_t ticket, int32_t* done, int32_t timeout_us) {
-  (void)timeout_us;
-  if (!c || !done) return CSO_ERR_ARG;
-  *done = 0;
-  for (size_t i = 0; i < c->finished.size(); ++i)
-    if (c->finished[i].first == ticket) {
-      *done = 1;
-      return c->finished[i].second;
-    }
-  bool known = false;
-  for (auto& r : c->queue) known |= r.ticket == ticket;
-  if (!known) {
-    cso_set_error("unknown ticket %llu", (unsigned long long)ticket);
-    return CSO_ERR_STATE;
-  }
-  // run queued requests up to and including this ticket
-  while (!c->queue.empty()) {
-    ServedReq r = c->queue.front();
-    c->queue.erase(c->queue.begin());
-    int rc = cso_find_groups(c, &r.in, &r.p, r.out);
-    c->finished.push_back({r.ticket, rc});
-    if (r.ticket == ticket) {
-      *done = 1;
-      return rc;
-    }
-  }
-  return CSO_ERR_STATE;
 }

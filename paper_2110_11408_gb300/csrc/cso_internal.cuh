@@ -29,8 +29,8 @@ void cso_set_error(const char* fmt, ...);
 static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // every kernel launch of the library passes its grid size through CL(), which
-// counts launches for cso_last_stats
-extern long long g_cso_launches;
+// counts the calling thread's launches for cso_last_stats
+extern thread_local long long g_cso_launches;
 template <class T>
 static inline T CL(T grid) {
   ++g_cso_launches;

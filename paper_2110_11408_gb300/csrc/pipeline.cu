@@ -598,7 +598,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   CSO_CUDA(cudaGetLastError());
 
   // per-halo rows and the catalogue
-  if ((size_t)H1 * 2 > c->rows_cap) {
+  if ((size_t)H1 * 2 + 1024 > c->rows_cap) {
     if (c->rows) {
       CSO_CUDA(cudaStreamSynchronize(st));
       CSO_CUDA(cudaFree(c->rows));

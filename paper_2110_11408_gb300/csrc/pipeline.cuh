@@ -10,12 +10,17 @@
 // device workspace per particle (all stages, worst case), bytes
 #define CSO_BYTES_PER_PARTICLE 440
 
-struct ServedReq {
+struct ServedRequest {
   cso_input in;
   cso_params p;
   cso_output* out;
-  uint64_t ticket;
+  uint64_t ticket = 0;
+  size_t need = 0;  // device bytes reserved while it runs
+  int status = CSO_OK;
+  bool done = false;
+  double t_submit = 0, t_start = 0, t_done = 0;  // host steady clock, seconds
 };
+struct ServedState;
 
 struct cso_ctx {
   int device = 0;
@@ -34,9 +39,12 @@ struct cso_ctx {
   cso_halo* rows = nullptr;  // per-halo rows (device), grown on demand
   size_t rows_cap = 0;
   uint64_t next_ticket = 0;
-  std::vector<ServedReq> queue;
-  std::vector<std::pair<uint64_t, int>> finished;
+  int served_slots = 0;           // worker slots of the served path (0 = 4)
+  ServedState* served = nullptr;  // created by the first cso_submit
 };
 
+size_t workspace_bytes(long long n, long long ncell, bool host_io);
 int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io);
+int check_io(const cso_input* in, const cso_params* p, cso_output* out);
+void served_stop(cso_ctx* c);
 int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out);
