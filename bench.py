@@ -115,6 +115,50 @@ def make_workload(name, seed_offset):
     raise SystemExit("unknown workload " + name)
 
 
+def served_stream(cso, torch, local, flags, n_req=24, n_distinct=6, mean_gap_s=0.020, seed=7):
+    """Poisson arrivals of boxes of the medium recipe at side 128 (2,097,152
+    particles each, the size of one 1/64 slab of a side-512 box) submitted to
+    the served path; latency = completion - scheduled arrival."""
+    from paper_2110_11408_gb300 import synth
+    rng = np.random.default_rng(seed)
+    data = [synth.medium_sample(side=128, seed=synth.SEED0 + 300 + k) for k in range(n_distinct)]
+    dev = [(torch.from_numpy(p).cuda(), torch.from_numpy(i.view(np.int64)).cuda(), m) for p, i, m in data]
+    gaps = rng.exponential(mean_gap_s, n_req)
+    out = {}
+    for label, arrivals in (("poisson", np.cumsum(gaps)), ("saturated", np.zeros(n_req))):
+        ctx = cso.Context(local, flags=flags | cso.FLAG_SLOTS(4))
+        # warm the slots (workspace growth happens once per slot)
+        warm = [cso.Buffers(dev[k % n_distinct][0], dev[k % n_distinct][1], True) for k in range(4)]
+        wt = [ctx.submit(b, cso.cso_params_default(dev[0][2]["u"])) for b in warm]
+        for t in wt:
+            ctx.wait(t)
+        bufs, tickets, sched = [], [], []
+        t0 = cso.cso_clock() + 0.01
+        for k in range(n_req):
+            pos, ids, meta = dev[k % n_distinct]
+            b = cso.Buffers(pos, ids, True)
+            target = t0 + arrivals[k]
+            while cso.cso_clock() < target:
+                pass
+            bufs.append(b)
+            sched.append(target)
+            tickets.append(ctx.submit(b, cso.cso_params_default(meta["u"])))
+        for t in tickets:
+            done, rc = ctx.wait(t)
+            assert done and rc == 0, cso.cso_last_error()
+        done_t = np.array([cso.cso_ticket_times(ctx.h, t)[2] for t in tickets])
+        lat = (done_t - np.array(sched)) * 1e3
+        n_tot = sum(len(dev[k % n_distinct][0]) for k in range(n_req))
+        span = done_t.max() - min(sched)
+        out[label] = {"requests": n_req, "particles_per_request": int(len(dev[0][0])), "slots": 4,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "particles_per_s": n_tot / span,
+                      "arrivals": ("Poisson, mean gap %.0f ms" % (mean_gap_s * 1e3)) if label == "poisson"
+                      else "all at t = 0"}
+        ctx.close()
+    return out
+
+
 def cpu_oracle_rate(samples):
     """Oracle (single thread) on bounded samples of the medium recipe."""
     import oracle as O
@@ -165,9 +209,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
-    ap.add_argument("--batched", action="store_true", help="batched CompaSO schedule")
+    ap.add_argument("--plain", action="store_true", help="time the plain schedule as the headline (default: batched)")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other schedule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -199,9 +245,8 @@ def main():
     pos, ids, meta = make_workload(args.workload, rank)
     n = len(pos)
     params = cso.cso_params_default(meta["u"])
-    flags = cso.FLAG_TIMING | (cso.FLAG_BATCHED if args.batched else 0)
-    ctx = cso.Context(local, flags=flags)
-    stream = torch.cuda.ExternalStream(cso.cso_stream(ctx.h))
+    primary = "plain" if args.plain else "batched"
+    flags = cso.FLAG_TIMING | (0 if args.plain else cso.FLAG_BATCHED)
     dpos = torch.from_numpy(pos).cuda()
     dids = torch.from_numpy(ids.view(np.int64)).cuda()
     buf = cso.Buffers(dpos, dids, on_device=True)
@@ -213,31 +258,46 @@ def main():
     stats = cso.cso_last_stats(cctx.h)
     cctx.close()
 
-    for _ in range(args.warmup):
-        cso.cso_find_groups(ctx.h, buf, params)
-    torch.cuda.synchronize()
-    barrier()
-
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    stage_acc = {}
-    with ClockSampler(local) as clk:
+    def time_schedule(fl, clk=None):
+        c = cso.Context(local, flags=fl)
+        stream = torch.cuda.ExternalStream(cso.cso_stream(c.h))
+        for _ in range(args.warmup):
+            cso.cso_find_groups(c.h, buf, params)
+        torch.cuda.synchronize()
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        acc = {}
+        if clk:
+            clk.__enter__()
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            cso.cso_find_groups(ctx.h, buf, params)
-            for k, v in cso.cso_stage_times(ctx.h).items():
-                stage_acc.setdefault(k, []).append(v)
+            cso.cso_find_groups(c.h, buf, params)
+            for k, v in cso.cso_stage_times(c.h).items():
+                acc.setdefault(k, []).append(v)
         ev1.record(stream)
         torch.cuda.synchronize()
-    barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    stats_t = cso.cso_last_stats(ctx.h)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        if clk:
+            clk.__exit__()
+        barrier()
+        t = ev0.elapsed_time(ev1) / args.steps
+        st = cso.cso_last_stats(c.h)
+        if dist is not None:
+            tt = torch.tensor([t], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return c, t, acc, st
+
+    clk = ClockSampler(local)
+    ctx, ms, stage_acc, stats_t = time_schedule(flags, clk)
     value = ws * n / (ms / 1e3)
+    other = None
+    if not args.no_compare:
+        c2, ms2, _, _ = time_schedule(cso.FLAG_TIMING | (cso.FLAG_BATCHED if args.plain else 0))
+        c2.close()
+        other = {"schedule": "batched" if args.plain else "plain", "value": ws * n / (ms2 / 1e3),
+                 "ms_per_step": ms2}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -270,6 +330,10 @@ def main():
         d2h = n * 8 * 4 + int(hb.cout.n_halos) * cso.HALO_DTYPE.itemsize
         e2e = {"value": ws * n / dt, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    served = None
+    if not args.no_served and ws == 1:
+        served = served_stream(cso, torch, local, flags & ~cso.FLAG_TIMING)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -296,9 +360,10 @@ def main():
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "n_particles": n,
-                   "schedule": "batched" if args.batched else "plain", "l2_flush": "working set > L2 (inputs 336 MB, "
+                   "schedule": primary, "l2_flush": "working set > L2 (inputs 336 MB, "
                    "cell table 1 GB)", "seed": meta["seed"]},
         "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "served": served, "other_schedule": other,
         "stages_ms": stages,
         "counts": {k: stats[k] for k in ("dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows",
                                          "pairs_b", "l1_work", "l2_work", "workspace_bytes")},
