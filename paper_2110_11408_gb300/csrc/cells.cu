@@ -11,63 +11,7 @@
 
 namespace {
 
-__device__ __forceinline__ int wrap_cell(int c, int nc, int& shift) {
-  shift = 0;
-  if (c < 0) {
-    shift = CSO_BOX;  // neighbour sits at the far end: move the query up by a box
-    return c + nc;
-  }
-  if (c >= nc) {
-    shift = -CSO_BOX;
-    return c - nc;
-  }
-  return c;
-}
-
-__device__ __forceinline__ int cell_of(int x, int nc) { return cell_coord(x, nc); }
-
-// Visit every cell-sorted index t in the 27-cell stencil of the query, row
-// by row (the three x-cells of a row are one contiguous run unless the row
-// wraps); f(t, xq, yq, zq) receives the query shifted by whole boxes so that
-// plain differences are minimum-image offsets.  No culling: lanes of a warp
-// in one cell walk the same runs, which keeps the warp converged.
-template <class F>
-__device__ __forceinline__ void for_stencil(const CellGrid& g, int x, int y, int z, F f) {
-  const int nc = g.nc;
-  const int cx = cell_of(x, nc), cy = cell_of(y, nc), cz = cell_of(z, nc);
-  for (int dz = -1; dz <= 1; ++dz) {
-    int sz;
-    const int zz = wrap_cell(cz + dz, nc, sz);
-    for (int dy = -1; dy <= 1; ++dy) {
-      int sy;
-      const int yy = wrap_cell(cy + dy, nc, sy);
-      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
-      const int yq = y + sy, zq = z + sz;
-      uint32_t lo0, hi0, lo1 = 0, hi1 = 0;
-      int sx1 = 0;
-      if (cx >= 1 && cx + 1 < nc) {
-        lo0 = row[cx - 1];
-        hi0 = row[cx + 2];
-      } else if (cx == 0) {
-        lo0 = row[0];
-        hi0 = row[2];
-        lo1 = row[nc - 1];
-        hi1 = row[nc];
-        sx1 = CSO_BOX;
-      } else {
-        lo0 = row[nc - 2];
-        hi0 = row[nc];
-        lo1 = row[0];
-        hi1 = row[1];
-        sx1 = -CSO_BOX;
-      }
-      for (uint32_t t = lo0; t < hi0; ++t) f(t, x, yq, zq);
-      for (uint32_t t = lo1; t < hi1; ++t) f(t, x + sx1, yq, zq);
-    }
-  }
-}
-
-__global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, int nc, uint32_t* __restrict__ key,
+__global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, CellGrid g, uint32_t* __restrict__ key,
                              uint32_t* __restrict__ rank, uint32_t* __restrict__ count, int* __restrict__ bad) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -76,19 +20,25 @@ __global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, int n
     atomicExch(bad, 1);
     x = y = z = 0;
   }
-  uint32_t k = ((uint32_t)cell_of(z, nc) * nc + cell_of(y, nc)) * nc + cell_of(x, nc);
+  // table column from the grid x (whole box or window alike)
+  int tc = g.colmap ? g.colmap[cell_coord(x, g.nc)] : cell_coord(x, g.nc);
+  if (tc < 0) {  // a window particle outside the window's columns
+    atomicExch(bad, 2);
+    tc = 0;
+  }
+  const uint32_t k = (uint32_t)grid_cell(g, cell_coord(z, g.nc), cell_coord(y, g.nc), tc);
   key[i] = k;
   rank[i] = atomicAdd(&count[k], 1u);
 }
 
 __global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n,
-                               const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+                               int x0, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
                                const uint32_t* __restrict__ start, int4* __restrict__ spos,
                                uint64_t* __restrict__ sid) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t dst = start[key[i]] + rank[i];
-  spos[dst] = make_int4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], (int)i);
+  spos[dst] = make_int4((pos[3 * i] - x0) & (CSO_BOX - 1), pos[3 * i + 1], pos[3 * i + 2], (int)i);
   sid[dst] = ids[i];
 }
 
@@ -100,9 +50,10 @@ __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_
 
 // Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2)
 __global__ void __launch_bounds__(256) k_density(CellGrid g, const int4* __restrict__ spos, int n, uint32_t b2,
-                                                 int include_self, long long* __restrict__ sigma) {
+                                                 int include_self, long long* __restrict__ sigma,
+                                                 const uint8_t* __restrict__ only) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
+  if (s >= n || (only && !only[s])) return;
   const int4 p = spos[s];
   unsigned long long acc = 0;
   for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) { acc += kern(spos[t], xq, yq, zq, b2); });
@@ -175,8 +126,7 @@ __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __re
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || parent[s] < 0) return;
   const int4 p = spos[s];
-  const int nc = g.nc;
-  const size_t cell = ((size_t)cell_of(p.z, nc) * nc + cell_of(p.y, nc)) * nc + cell_of(p.x, nc);
+  const size_t cell = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
   int linked = 0;
   for (uint32_t t = g.start[cell], e = g.start[cell + 1]; t < e && linked < 4; ++t) {
     if ((int)t == s) continue;
@@ -205,14 +155,14 @@ __global__ void k_cell_root_init(int* __restrict__ cell_root, long long ncell) {
   if (c < ncell) cell_root[c] = CELL_EMPTY;
 }
 
-__global__ void k_cell_root(const int4* __restrict__ spos, int n, int nc, const int* __restrict__ parent,
+__global__ void k_cell_root(const int4* __restrict__ spos, int n, CellGrid g, const int* __restrict__ parent,
                             int* __restrict__ cell_root) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int r = parent[s];
   if (r < 0) return;
   const int4 p = spos[s];
-  const size_t c = ((size_t)cell_of(p.z, nc) * nc + cell_of(p.y, nc)) * nc + cell_of(p.x, nc);
+  const size_t c = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
   int old = atomicCAS(&cell_root[c], CELL_EMPTY, r);
   if (old != CELL_EMPTY && old != r && old != CELL_MIXED) atomicExch(&cell_root[c], CELL_MIXED);
 }
@@ -229,18 +179,23 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
   if (s >= n || parent[s] < 0) return;
   const int4 p = spos[s];
   const int nc = g.nc;
-  const int cx = cell_of(p.x, nc), cy = cell_of(p.y, nc), cz = cell_of(p.z, nc);
+  const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc);
+  const XCells X = x_cells(g, grid_col(g, p.x));
+  // the x cells in order: left neighbour (or the wrapped far column), own, right
+  const int tc = grid_col(g, p.x);
+  const int xcol[3] = {X.a < tc ? X.a : X.wl, tc, X.b > tc ? X.b : X.wr};
+  const int xsh[3] = {X.a < tc ? 0 : CSO_BOX, 0, X.b > tc ? 0 : -CSO_BOX};
   int rs = uf_root(parent, s);
   for (int dz = -1; dz <= 1; ++dz) {
     int sz;
-    const int zz = wrap_cell(cz + dz, nc, sz);
+    const int zz = wrap_yz(cz + dz, nc, sz);
     for (int dy = -1; dy <= 1; ++dy) {
       int sy;
-      const int yy = wrap_cell(cy + dy, nc, sy);
-      for (int dx = -1; dx <= 1; ++dx) {
-        int sx;
-        const int xx = wrap_cell(cx + dx, nc, sx);
-        const size_t c = ((size_t)zz * nc + yy) * nc + xx;
+      const int yy = wrap_yz(cy + dy, nc, sy);
+      for (int k = 0; k < 3; ++k) {
+        if (xcol[k] < 0) continue;
+        const int sx = xsh[k];
+        const size_t c = grid_cell(g, zz, yy, xcol[k]);
         const int cr = cell_root[c];
         if (cr == CELL_EMPTY) continue;
         const bool unified = cr >= 0;
@@ -303,9 +258,9 @@ int cells_choose(long long b2, int* nc_out) {
   return CSO_OK;
 }
 
-int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint32_t* start, int4* spos,
-              uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st) {
-  long long ncell = (long long)nc * nc * nc;
+int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGrid& g, uint32_t* start,
+              int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st) {
+  long long ncell = (long long)g.ncols * g.nc * g.nc;
   size_t mark = ws.off;
   uint32_t* key = ws.get<uint32_t>(n);
   uint32_t* rank = ws.get<uint32_t>(n);
@@ -315,12 +270,12 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint
   }
   CSO_CUDA(cudaMemsetAsync(start, 0, sizeof(uint32_t) * (ncell + 1), st));
   if (n > 0) {
-    k_cell_count<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, n, nc, key, rank, start, bad);
+    k_cell_count<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, n, g, key, rank, start, bad);
     CSO_CUDA(cudaGetLastError());
   }
   CSO_TRY(scan_u32(start, ncell + 1, nullptr, ws, st));
   if (n > 0) {
-    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, key, rank, start, spos, sid);
+    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g.x0, key, rank, start, spos, sid);
     CSO_CUDA(cudaGetLastError());
   }
   ws.off = mark;
@@ -328,9 +283,9 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint
 }
 
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
-                  unsigned long long* pairs, cudaStream_t st) {
+                  unsigned long long* pairs, cudaStream_t st, const uint8_t* only) {
   if (n <= 0) return CSO_OK;
-  k_density<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma);
+  k_density<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, only);
   if (pairs) k_count_pairs<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, pairs);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;
@@ -340,12 +295,12 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
               const uint64_t* sid, int* parent, int* root, unsigned long long* minid, int* cell_root,
               cudaStream_t st) {
   if (n <= 0) return CSO_OK;
-  const long long ncell = (long long)g.nc * g.nc * g.nc;
+  const long long ncell = (long long)g.ncols * g.nc * g.nc;
   k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0);
   k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent);
   k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
   k_cell_root_init<<<CL(cdiv(ncell, 256)), 256, 0, st>>>(cell_root, ncell);
-  k_cell_root<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, n, g.nc, parent, cell_root);
+  k_cell_root<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, n, g, parent, cell_root);
   k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent, cell_root);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);

@@ -2,22 +2,39 @@
 #pragma once
 #include "cso_internal.cuh"
 
+// A cell table over the particles of a whole periodic box, or over a window
+// of x columns of one (the served slab stream).  Cells are at least as wide as
+// the largest search radius, so every neighbour lies in the 27 cells around a
+// particle's own.  Cell (cz, cy, column) starts at
+// start[(cz * nc + cy) * ncols + column]; the table has ncols * nc * nc + 1
+// entries, x fastest, so the x-cells of one (y, z) row are contiguous.
+//
+// Whole box: colmap == nullptr, ncols == nc, stored x is the grid x and x
+// wraps like y and z.  Window: colmap maps each global x column to its table
+// column (-1 if absent), cols maps back, and stored x is (grid x - x0) mod
+// 2^21: unwrapped across the window, which never spans half the box, so x
+// never wraps inside a window.
 struct CellGrid {
-  int nc;                 // cells per side
-  const uint32_t* start;  // nc^3 + 1 offsets into the cell-sorted arrays
+  int nc;
+  int ncols;
+  const uint32_t* start;
+  const int* colmap;
+  const int* cols;
+  int x0;
 };
 
-// One contiguous run [lo, hi) of the cell-sorted arrays inside the 27-cell
-// stencil of a query, with the query coordinates shifted by whole boxes so
-// that plain differences give minimum-image offsets for every particle of
-// the run.
-struct StencilRun {
-  uint32_t lo, hi;
-  int qx, qy, qz;
-};
+static inline CellGrid whole_box_grid(int nc, const uint32_t* start) {
+  return CellGrid{nc, nc, start, nullptr, nullptr, 0};
+}
 
 __device__ __forceinline__ int cell_coord(int x, int nc) {
   return (int)(((unsigned long long)(unsigned)x * (unsigned)nc) >> 21);
+}
+
+// table column of a stored x
+__device__ __forceinline__ int grid_col(const CellGrid& g, int xs) {
+  if (!g.colmap) return cell_coord(xs, g.nc);
+  return g.colmap[cell_coord((xs + g.x0) & (CSO_BOX - 1), g.nc)];
 }
 
 // first grid coordinate of cell c (cells are [ceil(c 2^21 / nc), ceil((c + 1) 2^21 / nc)))
@@ -25,82 +42,79 @@ __device__ __forceinline__ int cell_lo(int c, int nc) {
   return (int)(((long long)c * CSO_BOX + nc - 1) / nc);
 }
 
-// Visit every cell-sorted index t that can lie within squared radius r2 of
-// the query: the 27-cell stencil, minus the rows and the end cells of rows
-// whose nearest possible point is already at r2 or beyond (given the query's
-// offset inside its own cell).  f(t, xq, yq, zq) receives the query shifted by
-// whole boxes so that plain differences are minimum-image offsets; f returns
-// false to stop.  Requires cells at least as wide as the radius.
-template <class F>
-__device__ __forceinline__ void for_stencil_r(const CellGrid& g, int x, int y, int z, uint32_t r2, F f) {
-  const int nc = g.nc;
-  const int cx = cell_coord(x, nc), cy = cell_coord(y, nc), cz = cell_coord(z, nc);
-  // squared distance from the query to the near faces of the neighbouring cells
-  const long long xl = x - cell_lo(cx, nc) + 1, xr = cell_lo(cx + 1, nc) - x;
-  const long long yl = y - cell_lo(cy, nc) + 1, yr = cell_lo(cy + 1, nc) - y;
-  const long long zl = z - cell_lo(cz, nc) + 1, zr = cell_lo(cz + 1, nc) - z;
-  const long long R2 = r2;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const long long mz = dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0);
-    if (mz >= R2) continue;
-    int zz = cz + dz, sz = 0;
-    if (zz < 0) { zz += nc; sz = CSO_BOX; } else if (zz >= nc) { zz -= nc; sz = -CSO_BOX; }
-    for (int dy = -1; dy <= 1; ++dy) {
-      const long long my = mz + (dy < 0 ? yl * yl : (dy > 0 ? yr * yr : 0));
-      if (my >= R2) continue;
-      int yy = cy + dy, sy = 0;
-      if (yy < 0) { yy += nc; sy = CSO_BOX; } else if (yy >= nc) { yy -= nc; sy = -CSO_BOX; }
-      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
-      const bool left = my + xl * xl < R2, right = my + xr * xr < R2;
-      const int yq = y + sy, zq = z + sz;
-      // own cell, plus the x neighbours that can reach; wrapped ones are separate runs
-      int a = cx, b = cx;
-      int wl = -1, wr = -1;
-      if (left) { if (cx > 0) a = cx - 1; else wl = nc - 1; }
-      if (right) { if (cx + 1 < nc) b = cx + 1; else wr = 0; }
-      for (uint32_t t = row[a], e = row[b + 1]; t < e; ++t)
-        if (!f(t, x, yq, zq)) return;
-      if (wl >= 0)
-        for (uint32_t t = row[wl], e = row[wl + 1]; t < e; ++t)
-          if (!f(t, x + CSO_BOX, yq, zq)) return;
-      if (wr >= 0)
-        for (uint32_t t = row[0], e = row[1]; t < e; ++t)
-          if (!f(t, x - CSO_BOX, yq, zq)) return;
-    }
-  }
-}
+// The x cells around table column tc: columns a..b form one contiguous run
+// (a = tc - 1 and b = tc + 1 when those neighbours exist), and in a whole box
+// the row may wrap: wl >= 0 is the far-left column (query shifted by +box),
+// wr >= 0 the far-right one (query shifted by -box).
+struct XCells {
+  int a, b, wl, wr;
+};
 
-// The up to 18 runs (9 rows of three x-cells, split where a row wraps).
-__device__ __forceinline__ int stencil_runs(const CellGrid& g, int x, int y, int z, StencilRun* out) {
-  const int nc = g.nc;
-  const int cx = cell_coord(x, nc), cy = cell_coord(y, nc), cz = cell_coord(z, nc);
-  int r = 0;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int zz = cz + dz, sz = 0;
-    if (zz < 0) { zz += nc; sz = CSO_BOX; } else if (zz >= nc) { zz -= nc; sz = -CSO_BOX; }
-    for (int dy = -1; dy <= 1; ++dy) {
-      int yy = cy + dy, sy = 0;
-      if (yy < 0) { yy += nc; sy = CSO_BOX; } else if (yy >= nc) { yy -= nc; sy = -CSO_BOX; }
-      const uint32_t* row = g.start + ((size_t)zz * nc + yy) * nc;
-      if (cx >= 1 && cx + 1 < nc) {
-        out[r++] = StencilRun{row[cx - 1], row[cx + 2], x, y + sy, z + sz};
-      } else if (cx == 0) {
-        out[r++] = StencilRun{row[0], row[2], x, y + sy, z + sz};
-        out[r++] = StencilRun{row[nc - 1], row[nc], x + CSO_BOX, y + sy, z + sz};
-      } else {
-        out[r++] = StencilRun{row[nc - 2], row[nc], x, y + sy, z + sz};
-        out[r++] = StencilRun{row[0], row[1], x - CSO_BOX, y + sy, z + sz};
-      }
-    }
+__device__ __forceinline__ XCells x_cells(const CellGrid& g, int tc) {
+  XCells r{tc, tc, -1, -1};
+  if (!g.colmap) {
+    if (tc > 0) r.a = tc - 1; else r.wl = g.nc - 1;
+    if (tc + 1 < g.nc) r.b = tc + 1; else r.wr = 0;
+  } else {
+    const int gc = g.cols[tc];
+    if (tc > 0 && g.cols[tc - 1] == (gc + g.nc - 1) % g.nc) r.a = tc - 1;
+    if (tc + 1 < g.ncols && g.cols[tc + 1] == (gc + 1) % g.nc) r.b = tc + 1;
   }
   return r;
 }
 
+__device__ __forceinline__ int wrap_yz(int c, int nc, int& shift) {
+  shift = 0;
+  if (c < 0) {
+    shift = CSO_BOX;  // neighbour sits at the far end: move the query up by a box
+    return c + nc;
+  }
+  if (c >= nc) {
+    shift = -CSO_BOX;
+    return c - nc;
+  }
+  return c;
+}
+
+__device__ __forceinline__ const uint32_t* grid_row(const CellGrid& g, int zz, int yy) {
+  return g.start + ((size_t)zz * g.nc + yy) * g.ncols;
+}
+
+__device__ __forceinline__ size_t grid_cell(const CellGrid& g, int zz, int yy, int tc) {
+  return ((size_t)zz * g.nc + yy) * g.ncols + tc;
+}
+
+// Visit every cell-sorted index t in the 27-cell stencil of the query, row
+// by row; f(t, xq, yq, zq) receives the query shifted by whole boxes so that
+// plain differences are minimum-image offsets.  No culling: lanes of a warp
+// in one cell walk the same runs, which keeps the warp converged.
+template <class F>
+__device__ __forceinline__ void for_stencil(const CellGrid& g, int x, int y, int z, F f) {
+  const int nc = g.nc;
+  const int cy = cell_coord(y, nc), cz = cell_coord(z, nc);
+  const XCells X = x_cells(g, grid_col(g, x));
+  for (int dz = -1; dz <= 1; ++dz) {
+    int sz;
+    const int zz = wrap_yz(cz + dz, nc, sz);
+    for (int dy = -1; dy <= 1; ++dy) {
+      int sy;
+      const int yy = wrap_yz(cy + dy, nc, sy);
+      const uint32_t* row = grid_row(g, zz, yy);
+      const int yq = y + sy, zq = z + sz;
+      for (uint32_t t = row[X.a], e = row[X.b + 1]; t < e; ++t) f(t, x, yq, zq);
+      if (X.wl >= 0)
+        for (uint32_t t = row[X.wl], e = row[X.wl + 1]; t < e; ++t) f(t, x + CSO_BOX, yq, zq);
+      if (X.wr >= 0)
+        for (uint32_t t = row[X.wr], e = row[X.wr + 1]; t < e; ++t) f(t, x - CSO_BOX, yq, zq);
+    }
+  }
+}
+
 int cells_choose(long long b2, int* nc_out);
-int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, int nc, uint32_t* start, int4* spos,
-              uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st);
+int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGrid& g, uint32_t* start,
+              int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st);
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
-                  unsigned long long* pairs, cudaStream_t st);
+                  unsigned long long* pairs, cudaStream_t st, const uint8_t* only = nullptr);
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
               const uint64_t* sid, int* parent, int* root, unsigned long long* minid, int* cell_root,
               cudaStream_t st);

@@ -368,33 +368,32 @@ __device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
   const int4 p = a.spos[se];
   const long long sp = a.ssig[se];
   const uint64_t idp = a.sid[se];
-  const int nc = a.grid.nc;
-  const int cx = cell_coord(p.x, nc), cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc);
+  const CellGrid& g = a.grid;
+  const int nc = g.nc;
+  const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc);
+  const int tc = grid_col(g, p.x);
+  const XCells X = x_cells(g, tc);
   // lane r < 9 looks up row r = (dz + 1) * 3 + (dy + 1), dropping the rows and
   // end cells that cannot reach within b (one run, plus one where the row wraps)
   uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
   int qx1 = p.x, qy = p.y, qz = p.z;
   if (lane < 9) {
     const int dz = lane / 3 - 1, dy = lane % 3 - 1;
+    const int gx = (p.x + g.x0) & (CSO_BOX - 1), gcx = cell_coord(gx, nc);
     const long long zl = p.z - cell_lo(cz, nc) + 1, zr = cell_lo(cz + 1, nc) - p.z;
     const long long yl = p.y - cell_lo(cy, nc) + 1, yr = cell_lo(cy + 1, nc) - p.y;
-    const long long xl = p.x - cell_lo(cx, nc) + 1, xr = cell_lo(cx + 1, nc) - p.x;
+    const long long xl = gx - cell_lo(gcx, nc) + 1, xr = cell_lo(gcx + 1, nc) - gx;
     const long long m = (dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0)) + (dy < 0 ? yl * yl : (dy > 0 ? yr * yr : 0));
     if (m < (long long)a.b2) {
-      int zz = cz + dz, yy = cy + dy;
-      if (zz < 0) { zz += nc; qz += CSO_BOX; } else if (zz >= nc) { zz -= nc; qz -= CSO_BOX; }
-      if (yy < 0) { yy += nc; qy += CSO_BOX; } else if (yy >= nc) { yy -= nc; qy -= CSO_BOX; }
-      const uint32_t* row = a.grid.start + ((size_t)zz * nc + yy) * nc;
+      int sz, sy;
+      const int zz = wrap_yz(cz + dz, nc, sz), yy = wrap_yz(cy + dy, nc, sy);
+      qz += sz;
+      qy += sy;
+      const uint32_t* row = grid_row(g, zz, yy);
       const bool left = m + xl * xl < (long long)a.b2, right = m + xr * xr < (long long)a.b2;
-      int ca = cx, cb = cx;
-      if (left) {
-        if (cx > 0) ca = cx - 1;
-        else { lo1 = row[nc - 1]; hi1 = row[nc]; qx1 = p.x + CSO_BOX; }
-      }
-      if (right) {
-        if (cx + 1 < nc) cb = cx + 1;
-        else { lo1 = row[0]; hi1 = row[1]; qx1 = p.x - CSO_BOX; }
-      }
+      const int ca = left ? X.a : tc, cb = right ? X.b : tc;
+      if (left && X.wl >= 0) { lo1 = row[X.wl]; hi1 = row[X.wl + 1]; qx1 = p.x + CSO_BOX; }
+      if (right && X.wr >= 0) { lo1 = row[X.wr]; hi1 = row[X.wr + 1]; qx1 = p.x - CSO_BOX; }
       lo0 = row[ca];
       hi0 = row[cb + 1];
     }

@@ -19,20 +19,14 @@ namespace {
 
 constexpr unsigned long long NONE = ~0ull;
 
-struct Meta {  // device counters read back by the host
-  unsigned long long sigma_max, id_max;
-  unsigned long long pairs, work1, work2;
-  int bad;
-  unsigned pad;
-};
-
-__global__ void k_flags(const int* __restrict__ root, int n, uint32_t* __restrict__ dflag,
-                        uint32_t* __restrict__ rflag) {
+__global__ void k_flags(const int* __restrict__ root, int n, const uint8_t* __restrict__ select,
+                        uint32_t* __restrict__ dflag, uint32_t* __restrict__ rflag) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  int r = root[s];
-  dflag[s] = r >= 0;
-  rflag[s] = r == s;
+  const int r = root[s];
+  const bool in = r >= 0 && (!select || select[s]);
+  dflag[s] = in;
+  rflag[s] = in && r == s;
 }
 
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
@@ -49,7 +43,7 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 }
 
 // compact the dense particles; block maxima of Sigma and id, one atomic per block
-__global__ void __launch_bounds__(256) k_compact_dense(const int* __restrict__ root, int n,
+__global__ void __launch_bounds__(256) k_compact_dense(const uint32_t* __restrict__ dflag, int n,
                                                        const uint32_t* __restrict__ dscan,
                                                        const long long* __restrict__ sigma,
                                                        const uint64_t* __restrict__ sid, uint32_t* __restrict__ dl,
@@ -57,7 +51,7 @@ __global__ void __launch_bounds__(256) k_compact_dense(const int* __restrict__ r
   __shared__ unsigned long long sh[8];
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long ms = 0, mid = 0;
-  if (s < n && root[s] >= 0) {
+  if (s < n && dflag[s]) {
     dl[dscan[s]] = (uint32_t)s;
     ms = (unsigned long long)sigma[s];
     mid = (unsigned long long)sid[s];
@@ -217,7 +211,7 @@ __global__ void __launch_bounds__(256) k_summary(
     const int4* __restrict__ epos, const uint64_t* __restrict__ eid, const uint32_t* __restrict__ gs,
     const int* __restrict__ root, const unsigned long long* __restrict__ minid, const uint32_t* __restrict__ nnuc2,
     const uint32_t* __restrict__ hbase2, const uint32_t* __restrict__ hnuc2, const unsigned* __restrict__ h2size,
-    double inv_u, int np_min, cso_halo* __restrict__ rows, uint32_t* __restrict__ keep) {
+    double inv_u, int np_min, int x0, cso_halo* __restrict__ rows, uint32_t* __restrict__ keep) {
   __shared__ long long sh[8];
   const int h = blockIdx.x;
   const unsigned b = seg2[h];
@@ -252,7 +246,7 @@ __global__ void __launch_bounds__(256) k_summary(
   r.N = n;
   r.R2 = hR2[h];
   r.R_delta = sqrt((double)r.R2) * inv_u;
-  r.com[0] = wrap_box((double)pn.x + (double)sx / (double)n);
+  r.com[0] = wrap_box((double)((pn.x + x0) & (CSO_BOX - 1)) + (double)sx / (double)n);
   r.com[1] = wrap_box((double)pn.y + (double)sy / (double)n);
   r.com[2] = wrap_box((double)pn.z + (double)sz / (double)n);
   r.l0_id = minid[root[gs[kn]]];
@@ -262,7 +256,7 @@ __global__ void __launch_bounds__(256) k_summary(
     long long n2 = h2size[first2];
     r.l2max_id = eid[ek2[hnuc2[first2]]];
     r.l2max_N = n2;
-    r.l2max_com[0] = wrap_box((double)p2.x + (double)tx / (double)n2);
+    r.l2max_com[0] = wrap_box((double)((p2.x + x0) & (CSO_BOX - 1)) + (double)tx / (double)n2);
     r.l2max_com[1] = wrap_box((double)p2.y + (double)ty / (double)n2);
     r.l2max_com[2] = wrap_box((double)p2.z + (double)tz / (double)n2);
     for (int q = 0; q < nl2; ++q) {  // five largest sizes, descending
@@ -298,29 +292,6 @@ __global__ void k_catalogue_write(const cso_halo* __restrict__ rows, const uint3
   if (i < m) out[i] = rows[order[i]];
 }
 
-struct Stages {
-  cso_ctx* c;
-  bool on;
-  int k = 0;
-  void mark(const char* name) {
-    if (!on || k >= CSO_MAX_STAGES) return;
-    cudaEventRecord(c->ev[k], c->stream);
-    c->stage_name[k] = name;
-    ++k;
-  }
-  void finish() {
-    if (!on) return;
-    cudaEventRecord(c->ev[k], c->stream);
-    cudaEventSynchronize(c->ev[k]);
-    for (int i = 0; i < k; ++i) {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
-      c->stage_ms[i] = ms;
-    }
-    c->nstages = k;
-  }
-};
-
 int readback(cso_ctx* c, const void* dev, size_t bytes) {
   CSO_CUDA(cudaMemcpyAsync(c->pinned, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
   CSO_CUDA(cudaStreamSynchronize(c->stream));
@@ -331,82 +302,33 @@ int readback(cso_ctx* c, const void* dev, size_t bytes) {
 
 }  // namespace
 
-int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out) {
+int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, Meta* meta, uint64_t* ol1,
+               uint64_t* ol2, cso_halo** rows_out, int* nrows_out) {
   cudaStream_t st = c->stream;
-  const long long n = in->n;
-  memset(c->stats, 0, sizeof(c->stats));
-  c->stats[0] = n;
-  const long long launches0 = g_cso_launches;
-  c->nstages = 0;
-  out->n_halos = 0;
-  if (n == 0) return CSO_OK;
-  int nc;
-  CSO_TRY(cells_choose(p->b2, &nc));
-  const long long ncell = (long long)nc * nc * nc;
-  const bool host_in = !in->on_device, host_out = !out->on_device;
-  CSO_TRY(ctx_reserve(c, n, ncell, host_in || host_out));
   Workspace& ws = c->ws;
-  Stages S{c, (c->flags & CSO_FLAG_TIMING) != 0};
-  const int N = (int)n;
-
+  const CellGrid& g = *gi.g;
+  const int4* spos = gi.spos;
+  const long long* sigma = gi.sigma;
+  const uint64_t* sid = gi.sid;
+  const int* root = gi.root;
+  const unsigned long long* minid = gi.minid;
+  const int N = gi.n;
+  const long long n = gi.n;
 #define ALLOC(T, name, cnt)                              \
   T* name = ws.get<T>(cnt);                              \
   if (!name) {                                           \
     cso_set_error("workspace exhausted (%s)", #name);    \
     return CSO_ERR_BUDGET;                               \
   }
-
-  // ---- inputs ----
-  S.mark("h2d");
-  const int32_t* pos = in->pos;
-  const uint64_t* ids = in->ids;
-  if (host_in) {
-    ALLOC(int32_t, dpos, 3 * n);
-    ALLOC(uint64_t, dids, n);
-    CSO_CUDA(cudaMemcpyAsync(dpos, in->pos, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, st));
-    CSO_CUDA(cudaMemcpyAsync(dids, in->ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
-    pos = dpos;
-    ids = dids;
-  }
-  ALLOC(Meta, meta, 1);
-  CSO_CUDA(cudaMemsetAsync(meta, 0, sizeof(Meta), st));
-
-  // ---- bin ----
-  S.mark("bin");
-  ALLOC(uint32_t, start, ncell + 1);
-  ALLOC(int4, spos, n);
-  ALLOC(uint64_t, sid, n);
-  CSO_TRY(cells_bin(pos, ids, n, nc, start, spos, sid, &meta->bad, ws, st));
-  CellGrid g{nc, start};
-
-  // ---- density ----
-  S.mark("density");
-  ALLOC(long long, sigma, n);
-  const bool count_pairs = (c->flags & CSO_FLAG_COUNT_PAIRS) != 0;
-  CSO_TRY(cells_density(g, spos, N, (uint32_t)p->b2, p->include_self, sigma, count_pairs ? &meta->pairs : nullptr,
-                        st));
-
-  // ---- fof ----
-  S.mark("fof");
-  ALLOC(int, parent, n);
-  ALLOC(int, root, n);
-  ALLOC(unsigned long long, minid, n);
-  {
-    size_t mark = ws.off;
-    ALLOC(int, cell_root, ncell);  // per-cell tree summary, transient
-    CSO_TRY(cells_fof(g, spos, N, sigma, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, cell_root, st));
-    ws.off = mark;
-  }
-
   // ---- gather: dense particles by (group, Sigma desc, id asc) ----
   S.mark("gather");
   ALLOC(uint32_t, dscan, n + 1);
   ALLOC(uint32_t, rscan, n + 1);
-  k_flags<<<G1(n)>>>(root, N, dscan, rscan);
+  k_flags<<<G1(n)>>>(root, N, gi.select, dscan, rscan);
   CSO_TRY(scan_u32(dscan, n, dscan + n, ws, st));
   CSO_TRY(scan_u32(rscan, n, rscan + n, ws, st));
   ALLOC(uint32_t, dl, n);
-  k_compact_dense<<<G1(n)>>>(root, N, dscan, sigma, sid, dl, meta);
+  k_compact_dense<<<G1(n)>>>(dscan, N, dscan, sigma, sid, dl, meta);
   CSO_CUDA(cudaGetLastError());
   // counters: n_dense, G, sigma_max, id_max, bad
   {
@@ -425,7 +347,6 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   }
   c->stats[1] = nd;
   c->stats[2] = G;
-  if (count_pairs) c->stats[6] = (int64_t)hm.pairs;
 
   const int bits_id = bit_length_u64(hm.id_max);
   const int bits_sig = nd ? bit_length_u64(hm.sigma_max - (unsigned long long)(p->T_L0 + 1)) : 0;
@@ -567,7 +488,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   else CSO_TRY(level_run(L2, st));
 
   // ---- output ----
-  S.mark("output");
+  S.mark("halos");
   ALLOC(uint32_t, hbase2, H1 + 1);
   if (H1 > 0) CSO_CUDA(cudaMemcpyAsync(hbase2, nnuc2, sizeof(uint32_t) * H1, cudaMemcpyDeviceToDevice, st));
   CSO_TRY(scan_u32(hbase2, H1, hbase2 + H1, ws, st));
@@ -582,17 +503,6 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   CSO_TRY(level_halo(H1, seg2, nnuc2, hbase2, eslot2, nucm2, nucR22, ehalo2, hnuc2, hR2b, hseg2, st));
   if (H2 > 0) CSO_CUDA(cudaMemsetAsync(h2size, 0, sizeof(unsigned) * H2, st));
 
-  uint64_t *ol0 = out->l0, *ol1 = out->l1, *ol2 = out->l2;
-  int64_t* osig = out->sigma;
-  if (host_out) {
-    if (ol0) { ALLOC(uint64_t, t, n); ol0 = t; }
-    if (ol1) { ALLOC(uint64_t, t, n); ol1 = t; }
-    if (ol2) { ALLOC(uint64_t, t, n); ol2 = t; }
-    if (osig) { ALLOC(int64_t, t, n); osig = t; }
-  }
-  if (ol1) k_fill_u64<<<G1(n)>>>(ol1, n, NONE);
-  if (ol2) k_fill_u64<<<G1(n)>>>(ol2, n, NONE);
-  k_out_cells<<<G1(n)>>>(spos, N, sigma, root, minid, osig, ol0);
   if (ol1 && nd > 0) k_out_l1<<<G1(nd)>>>(ehalo, nd, gs, spos, hnuc, eid, ol1);
   if (na > 0) k_out_l2<<<G1(na)>>>(ehalo2, na, ek2, gs, spos, hnuc2, eid, ol2, h2size);
   CSO_CUDA(cudaGetLastError());
@@ -614,7 +524,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   int nrows = 0;
   if (H1 > 0) {
     k_summary<<<CL(H1), 256, 0, st>>>(seg2, epos2, ehalo2, ek2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2,
-                                   h2size, 1.0 / p->l_mean_grid, p->np_min_L1, rows, keep);
+                                   h2size, 1.0 / p->l_mean_grid, p->np_min_L1, gi.x0, rows, keep);
     CSO_CUDA(cudaGetLastError());
     ALLOC(uint32_t, kscan, H1 + 1);
     CSO_CUDA(cudaMemcpyAsync(kscan, keep, sizeof(uint32_t) * H1, cudaMemcpyDeviceToDevice, st));
@@ -635,6 +545,105 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
       CSO_CUDA(cudaGetLastError());
     }
   }
+  *rows_out = sorted_rows;
+  *nrows_out = nrows;
+#undef ALLOC
+  return CSO_OK;
+}
+
+int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out) {
+  cudaStream_t st = c->stream;
+  const long long n = in->n;
+  memset(c->stats, 0, sizeof(c->stats));
+  c->stats[0] = n;
+  const long long launches0 = g_cso_launches;
+  c->nstages = 0;
+  out->n_halos = 0;
+  if (n == 0) return CSO_OK;
+  int nc;
+  CSO_TRY(cells_choose(p->b2, &nc));
+  const long long ncell = (long long)nc * nc * nc;
+  const bool host_in = !in->on_device, host_out = !out->on_device;
+  CSO_TRY(ctx_reserve(c, n, ncell, host_in || host_out));
+  Workspace& ws = c->ws;
+  Stages S{c, (c->flags & CSO_FLAG_TIMING) != 0};
+  const int N = (int)n;
+
+#define ALLOC(T, name, cnt)                              \
+  T* name = ws.get<T>(cnt);                              \
+  if (!name) {                                           \
+    cso_set_error("workspace exhausted (%s)", #name);    \
+    return CSO_ERR_BUDGET;                               \
+  }
+
+  // ---- inputs ----
+  S.mark("h2d");
+  const int32_t* pos = in->pos;
+  const uint64_t* ids = in->ids;
+  if (host_in) {
+    ALLOC(int32_t, dpos, 3 * n);
+    ALLOC(uint64_t, dids, n);
+    CSO_CUDA(cudaMemcpyAsync(dpos, in->pos, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, st));
+    CSO_CUDA(cudaMemcpyAsync(dids, in->ids, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
+    pos = dpos;
+    ids = dids;
+  }
+  ALLOC(Meta, meta, 1);
+  CSO_CUDA(cudaMemsetAsync(meta, 0, sizeof(Meta), st));
+
+  // ---- bin ----
+  S.mark("bin");
+  ALLOC(uint32_t, start, ncell + 1);
+  ALLOC(int4, spos, n);
+  ALLOC(uint64_t, sid, n);
+  CellGrid g = whole_box_grid(nc, start);
+  CSO_TRY(cells_bin(pos, ids, n, g, start, spos, sid, &meta->bad, ws, st));
+
+  // ---- density ----
+  S.mark("density");
+  ALLOC(long long, sigma, n);
+  const bool count_pairs = (c->flags & CSO_FLAG_COUNT_PAIRS) != 0;
+  CSO_TRY(cells_density(g, spos, N, (uint32_t)p->b2, p->include_self, sigma, count_pairs ? &meta->pairs : nullptr,
+                        st));
+
+  // ---- fof ----
+  S.mark("fof");
+  ALLOC(int, parent, n);
+  ALLOC(int, root, n);
+  ALLOC(unsigned long long, minid, n);
+  {
+    size_t mark = ws.off;
+    ALLOC(int, cell_root, ncell);  // per-cell tree summary, transient
+    CSO_TRY(cells_fof(g, spos, N, sigma, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, cell_root, st));
+    ws.off = mark;
+  }
+
+  // ---- outputs in input order ----
+  uint64_t *ol0 = out->l0, *ol1 = out->l1, *ol2 = out->l2;
+  int64_t* osig = out->sigma;
+  if (host_out) {
+    if (ol0) { ALLOC(uint64_t, t, n); ol0 = t; }
+    if (ol1) { ALLOC(uint64_t, t, n); ol1 = t; }
+    if (ol2) { ALLOC(uint64_t, t, n); ol2 = t; }
+    if (osig) { ALLOC(int64_t, t, n); osig = t; }
+  }
+  if (ol1) k_fill_u64<<<G1(n)>>>(ol1, n, NONE);
+  if (ol2) k_fill_u64<<<G1(n)>>>(ol2, n, NONE);
+
+  GroupsIn gin{&g, spos, sigma, sid, root, minid, nullptr, N, 0};
+  int nrows = 0;
+  cso_halo* sorted_rows = nullptr;
+  CSO_TRY(run_groups(c, p, gin, S, meta, ol1, ol2, &sorted_rows, &nrows));
+  if (count_pairs) {
+    Meta hm2;
+    CSO_CUDA(cudaMemcpyAsync(c->pinned, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
+    CSO_CUDA(cudaStreamSynchronize(st));
+    memcpy(&hm2, c->pinned, sizeof(Meta));
+    c->stats[6] = (int64_t)hm2.pairs;
+  }
+  S.mark("output");
+  k_out_cells<<<G1(n)>>>(spos, N, sigma, root, minid, osig, ol0);
+  CSO_CUDA(cudaGetLastError());
   out->n_halos = nrows;
   c->stats[5] = nrows;
   const int ncopy = nrows <= out->halo_cap ? nrows : 0;
@@ -653,6 +662,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   S.finish();
   CSO_CUDA(cudaMemcpyAsync(c->pinned, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
   CSO_CUDA(cudaStreamSynchronize(st));
+  Meta hm;
   memcpy(&hm, c->pinned, sizeof(Meta));
   c->stats[7] = (int64_t)hm.work1;
   c->stats[8] = (int64_t)hm.work2;

@@ -3,7 +3,7 @@
 #include <utility>
 #include <vector>
 
-#include "cso_internal.cuh"
+#include "cells.cuh"
 
 #define CSO_MAX_STAGES 16
 #define CSO_NSTATS 11
@@ -42,6 +42,57 @@ struct cso_ctx {
   int served_slots = 0;           // worker slots of the served path (0 = 4)
   ServedState* served = nullptr;  // created by the first cso_submit
 };
+
+struct Meta {  // device counters read back by the host
+  unsigned long long sigma_max, id_max;
+  unsigned long long pairs, work1, work2;
+  int bad;
+  unsigned pad;
+};
+
+// dense particles taking part (all, or those of selected groups) and group roots
+struct Stages {
+  cso_ctx* c;
+  bool on;
+  int k = 0;
+  void mark(const char* name) {
+    if (!on || k >= CSO_MAX_STAGES) return;
+    cudaEventRecord(c->ev[k], c->stream);
+    c->stage_name[k] = name;
+    ++k;
+  }
+  void finish() {
+    if (!on) return;
+    cudaEventRecord(c->ev[k], c->stream);
+    cudaEventSynchronize(c->ev[k]);
+    for (int i = 0; i < k; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+      c->stage_ms[i] = ms;
+    }
+    c->nstages = k;
+  }
+};
+
+// inputs of the group stages: cell-sorted particles with their kernel sums
+// and L0 roots; with `select`, only dense particles whose select flag is set
+// (whole groups) take part.  x0 is added to stored x for the catalogue.
+struct GroupsIn {
+  const CellGrid* g;
+  const int4* spos;
+  const long long* sigma;
+  const uint64_t* sid;
+  const int* root;
+  const unsigned long long* minid;
+  const uint8_t* select;
+  int n;
+  int x0;
+};
+
+// gather, L1, L2, labels (ol1 / ol2 indexed by spos[s].w, may be null) and
+// the catalogue rows (device, increasing nucleus id) of the groups taking part
+int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, Meta* meta, uint64_t* ol1,
+               uint64_t* ol2, cso_halo** rows_out, int* nrows_out);
 
 size_t workspace_bytes(long long n, long long ncell, bool host_io);
 int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io);
