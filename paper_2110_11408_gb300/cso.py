@@ -182,36 +182,39 @@ def _ptr(x):
 class Buffers:
     """Inputs/outputs of one request: torch CUDA tensors or numpy arrays."""
 
-    def __init__(self, pos, ids, on_device, halo_cap=None, want=("l0", "l1", "l2", "sigma")):
+    def __init__(self, pos, ids, on_device, halo_cap=None, want=("l0", "l1", "l2", "sigma"), x_lo=0, x_hi=0,
+                 request_id=0, out_device=None):
         n = int(pos.shape[0])
         self.n = n
         self.on_device = on_device
+        self.out_device = on_device if out_device is None else bool(out_device)
         self.halo_cap = int(halo_cap if halo_cap is not None else max(16, n // 35 + 1))
         self.pos, self.ids = pos, ids
-        if on_device:
+        if self.out_device:
             import torch
-            dev = pos.device
+            dev = pos.device if on_device else torch.device("cuda", torch.cuda.current_device())
             mk = lambda: torch.empty(n, dtype=torch.int64, device=dev)
             self.halos = torch.empty(self.halo_cap * HALO_DTYPE.itemsize, dtype=torch.uint8, device=dev)
         else:
             mk = lambda: np.empty(n, np.uint64)
             self.halos = np.empty(self.halo_cap, HALO_DTYPE)
         self.out = {k: mk() for k in want}
-        self.cin = CsoInput(pos=_ptr(pos), ids=_ptr(ids), n=n, on_device=int(on_device), x_lo=0, x_hi=0,
-                            request_id=0)
+        # x_hi > 0: the x-slab [x_lo, x_hi) of a box streamed under `request_id`
+        self.cin = CsoInput(pos=_ptr(pos), ids=_ptr(ids), n=n, on_device=int(on_device), x_lo=int(x_lo),
+                            x_hi=int(x_hi), request_id=int(request_id))
         self.cout = CsoOutput(l0=_ptr(self.out.get("l0")), l1=_ptr(self.out.get("l1")),
                               l2=_ptr(self.out.get("l2")), sigma=_ptr(self.out.get("sigma")),
                               halos=_ptr(self.halos), halo_cap=self.halo_cap, n_halos=0,
-                              on_device=int(on_device))
+                              on_device=int(self.out_device))
 
     def result(self):
         """Outputs as numpy (copies device tensors to the host)."""
         r = {}
         for k, v in self.out.items():
-            a = v.cpu().numpy() if self.on_device else v
+            a = v.cpu().numpy() if self.out_device else v
             r[k] = a.view(np.int64) if k == "sigma" else a.view(np.uint64)
         nh = int(self.cout.n_halos)
-        if self.on_device:
+        if self.out_device:
             raw = self.halos[: min(nh, self.halo_cap) * HALO_DTYPE.itemsize].cpu().numpy()
             r["halos"] = raw.view(HALO_DTYPE).copy()
         else:

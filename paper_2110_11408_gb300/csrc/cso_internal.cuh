@@ -20,6 +20,7 @@ void cso_set_error(const char* fmt, ...);
       return CSO_ERR_CUDA;                                                             \
     }                                                                                  \
   } while (0)
+#define CSO_CUDA_VOID(call) (void)(call)
 #define CSO_TRY(expr)          \
   do {                         \
     int rc_ = (expr);          \

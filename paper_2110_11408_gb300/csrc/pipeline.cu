@@ -43,15 +43,15 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v
 }
 
 // compact the dense particles; block maxima of Sigma and id, one atomic per block
-__global__ void __launch_bounds__(256) k_compact_dense(const uint32_t* __restrict__ dflag, int n,
-                                                       const uint32_t* __restrict__ dscan,
+__global__ void __launch_bounds__(256) k_compact_dense(const int* __restrict__ root, const uint8_t* __restrict__ select,
+                                                       int n, const uint32_t* __restrict__ dscan,
                                                        const long long* __restrict__ sigma,
                                                        const uint64_t* __restrict__ sid, uint32_t* __restrict__ dl,
                                                        Meta* meta) {
   __shared__ unsigned long long sh[8];
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long ms = 0, mid = 0;
-  if (s < n && dflag[s]) {
+  if (s < n && root[s] >= 0 && (!select || select[s])) {
     dl[dscan[s]] = (uint32_t)s;
     ms = (unsigned long long)sigma[s];
     mid = (unsigned long long)sid[s];
@@ -286,10 +286,15 @@ __global__ void k_catalogue_keys(const cso_halo* __restrict__ rows, const uint32
   val[kscan[h]] = (uint32_t)h;
 }
 
+// rows in nucleus-id order; optionally the input index of each row's nucleus
 __global__ void k_catalogue_write(const cso_halo* __restrict__ rows, const uint32_t* __restrict__ order, int m,
-                                  cso_halo* __restrict__ out) {
+                                  const uint32_t* __restrict__ hnuc, const int4* __restrict__ epos,
+                                  cso_halo* __restrict__ out, uint32_t* __restrict__ out_w) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) out[i] = rows[order[i]];
+  if (i >= m) return;
+  const uint32_t h = order[i];
+  out[i] = rows[h];
+  if (out_w) out_w[i] = (uint32_t)epos[hnuc[h]].w;
 }
 
 int readback(cso_ctx* c, const void* dev, size_t bytes) {
@@ -303,7 +308,7 @@ int readback(cso_ctx* c, const void* dev, size_t bytes) {
 }  // namespace
 
 int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, Meta* meta, uint64_t* ol1,
-               uint64_t* ol2, cso_halo** rows_out, int* nrows_out) {
+               uint64_t* ol2, cso_halo** rows_out, int* nrows_out, uint32_t** rows_w_out) {
   cudaStream_t st = c->stream;
   Workspace& ws = c->ws;
   const CellGrid& g = *gi.g;
@@ -328,7 +333,7 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   CSO_TRY(scan_u32(dscan, n, dscan + n, ws, st));
   CSO_TRY(scan_u32(rscan, n, rscan + n, ws, st));
   ALLOC(uint32_t, dl, n);
-  k_compact_dense<<<G1(n)>>>(dscan, N, dscan, sigma, sid, dl, meta);
+  k_compact_dense<<<G1(n)>>>(root, gi.select, N, dscan, sigma, sid, dl, meta);
   CSO_CUDA(cudaGetLastError());
   // counters: n_dense, G, sigma_max, id_max, bad
   {
@@ -541,7 +546,13 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
       uint64_t* pl = ckey;
       uint32_t* pv = cval;
       CSO_TRY(radix_sort_128(&ph, &pl, &pv, nullptr, ckey2, cval2, nrows, bit_length_u64(hm.id_max), ws, st));
-      k_catalogue_write<<<G1(nrows)>>>(rows, pv, nrows, sorted_rows);
+      uint32_t* row_w = nullptr;
+      if (rows_w_out) {
+        ALLOC(uint32_t, rw, nrows);
+        row_w = rw;
+        *rows_w_out = rw;
+      }
+      k_catalogue_write<<<G1(nrows)>>>(rows, pv, nrows, hnuc, epos, sorted_rows, row_w);
       CSO_CUDA(cudaGetLastError());
     }
   }
@@ -633,7 +644,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   GroupsIn gin{&g, spos, sigma, sid, root, minid, nullptr, N, 0};
   int nrows = 0;
   cso_halo* sorted_rows = nullptr;
-  CSO_TRY(run_groups(c, p, gin, S, meta, ol1, ol2, &sorted_rows, &nrows));
+  CSO_TRY(run_groups(c, p, gin, S, meta, ol1, ol2, &sorted_rows, &nrows, nullptr));
   if (count_pairs) {
     Meta hm2;
     CSO_CUDA(cudaMemcpyAsync(c->pinned, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));

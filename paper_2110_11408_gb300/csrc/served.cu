@@ -17,6 +17,7 @@
 
 #include "cells.cuh"
 #include "pipeline.cuh"
+#include "stream.cuh"
 
 struct ServedState {
   std::mutex mu;
@@ -25,6 +26,7 @@ struct ServedState {
   std::deque<ServedRequest*> queue;
   std::unordered_map<uint64_t, ServedRequest*> tickets;
   std::vector<cso_ctx*> slots;
+  std::unordered_map<uint64_t, StreamState*> streams;  // slab streams by request_id
   std::vector<std::thread> workers;
   size_t in_use = 0;  // device bytes reserved by running requests
   bool stop = false;
@@ -43,8 +45,89 @@ static size_t request_bytes(const cso_input* in, const cso_params* p, const cso_
   int nc = 0;
   *rc = cells_choose(q.b2, &nc);
   if (*rc != CSO_OK) return 0;
+  if (in->x_hi > 0) {
+    // a slab: its window holds the slab, its ghosts and the open groups
+    // behind it; budget three slabs' worth of particles over the slab's
+    // columns and a margin
+    const long long cols = (long long)(in->x_hi - in->x_lo) * nc / CSO_BOX + 8;
+    return workspace_bytes(3 * in->n + 4096, (cols < nc ? cols : nc) * nc * nc, false);
+  }
   return workspace_bytes(in->n, (long long)nc * nc * nc, !in->on_device || !out->on_device) +
          (size_t)(in->n / 16 + 1024) * 2 * sizeof(cso_halo);
+}
+
+static bool is_slab(const ServedRequest* r) { return r->in.x_hi > 0; }
+
+// First admissible request in submission order: a whole box whose workspace
+// fits the budget next to the running ones (none may overtake a whole box that
+// does not fit yet), or a slab whose stream is not being worked on.
+static std::deque<ServedRequest*>::iterator pick(ServedState& S, size_t budget) {
+  for (auto it = S.queue.begin(); it != S.queue.end(); ++it) {
+    ServedRequest* r = *it;
+    const bool fits = budget == 0 || S.in_use + r->need <= budget;
+    if (!is_slab(r)) {
+      if (fits) return it;
+      return S.queue.end();
+    }
+    auto st = S.streams.find(r->in.request_id);
+    const bool busy = st != S.streams.end() && st->second->busy;
+    if (!busy && fits) return it;
+  }
+  return S.queue.end();
+}
+
+static void finish(ServedRequest* r, int rc, double t) {
+  r->status = rc;
+  r->t_done = t;
+  r->done = true;
+}
+
+static void run_slab(cso_ctx* slot, ServedState& S, ServedRequest* r) {
+  StreamState* ss = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(S.mu);
+    auto it = S.streams.find(r->in.request_id);
+    if (it != S.streams.end()) ss = it->second;
+  }
+  int rc = CSO_OK;
+  if (!ss) {
+    cso_set_error("a slab stream must start at x = 0");
+    rc = CSO_ERR_STATE;
+  }
+  if (rc == CSO_OK && ss->failed) {
+    cso_set_error("an earlier slab of this stream failed");
+    rc = CSO_ERR_STATE;
+  }
+  if (rc == CSO_OK) {
+    CSO_CUDA_VOID(cudaSetDevice(slot->device));
+    rc = stream_step(slot, *ss, &r->in, r->out, r);
+    if (rc != CSO_OK) ss->failed = true;
+  }
+  std::lock_guard<std::mutex> lock(S.mu);
+  const double t = now_s();
+  if (rc != CSO_OK) {
+    finish(r, rc, t);
+    if (ss) {  // every pending slab of a failed stream fails with it
+      for (auto& sl : ss->slabs)
+        if (!sl.completed && sl.req && !sl.req->done) finish(sl.req, CSO_ERR_STATE, t);
+    }
+  } else {
+    bool all = true;
+    for (auto& sl : ss->slabs) {
+      if (sl.newly_completed) {
+        sl.newly_completed = false;
+        sl.req->out->n_halos = sl.n_halos;
+        finish(sl.req, sl.n_halos > sl.out.halo_cap ? CSO_ERR_CAPACITY : CSO_OK, t);
+      }
+      all = all && sl.completed;
+    }
+    if (all && ss->x_received == CSO_BOX) {  // the stream is over
+      S.streams.erase(ss->id);
+      stream_release(ss);
+      ss = nullptr;
+    }
+  }
+  if (ss) ss->busy = false;
 }
 
 static void worker_loop(cso_ctx* parent, int k) {
@@ -54,27 +137,36 @@ static void worker_loop(cso_ctx* parent, int k) {
     ServedRequest* r = nullptr;
     {
       std::unique_lock<std::mutex> lock(S.mu);
-      S.cv_work.wait(lock, [&] {
-        if (S.stop) return true;
-        if (S.queue.empty()) return false;
-        // first come, first served: only the head may be admitted
-        const size_t need = S.queue.front()->need;
-        return parent->budget == 0 || S.in_use + need <= parent->budget;
-      });
+      S.cv_work.wait(lock, [&] { return S.stop || pick(S, parent->budget) != S.queue.end(); });
       if (S.stop) return;
-      r = S.queue.front();
-      S.queue.pop_front();
+      auto it = pick(S, parent->budget);
+      r = *it;
+      S.queue.erase(it);
       S.in_use += r->need;
       r->t_start = now_s();
+      if (is_slab(r)) {
+        auto st = S.streams.find(r->in.request_id);
+        if (st != S.streams.end()) {
+          st->second->busy = true;
+        } else if (r->in.x_lo == 0) {  // the first slab opens the stream
+          StreamState* ss = nullptr;
+          if (stream_begin(&ss, r->in.request_id, &r->p) == CSO_OK) {
+            ss->busy = true;
+            S.streams[r->in.request_id] = ss;
+          }
+        }
+      }
     }
-    // idle slots keep their workspace for the next request; the budget
-    // counts what running requests reserve
-    int rc = cso_find_groups(slot, &r->in, &r->p, r->out);
-    {
+    if (is_slab(r)) {
+      run_slab(slot, S, r);
       std::lock_guard<std::mutex> lock(S.mu);
-      r->status = rc;
-      r->t_done = now_s();
-      r->done = true;
+      S.in_use -= r->need;
+    } else {
+      // idle slots keep their workspace for the next request; the budget
+      // counts what running requests reserve
+      int rc = cso_find_groups(slot, &r->in, &r->p, r->out);
+      std::lock_guard<std::mutex> lock(S.mu);
+      finish(r, rc, now_s());
       S.in_use -= r->need;
     }
     S.cv_done.notify_all();
@@ -107,6 +199,7 @@ void served_stop(cso_ctx* c) {
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
   for (auto* s : S->slots) cso_free(s);
+  for (auto& kv : S->streams) stream_release(kv.second);
   for (auto& kv : S->tickets) delete kv.second;
   for (auto* r : S->queue) (void)r;  // owned through the ticket table
   delete S;
