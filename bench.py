@@ -159,6 +159,53 @@ def served_stream(cso, torch, local, flags, n_req=24, n_distinct=6, mean_gap_s=0
     return out
 
 
+def slab_stream(cso, torch, local, flags, pos, ids, meta, n_slabs=64, mean_gap_s=0.020, seed=11):
+    """The benchmark box delivered as n_slabs x-slabs in order (ghost columns
+    and open L0 groups stay on the device between slabs).  Latency = the time
+    from a slab's scheduled arrival until all its particles have final labels;
+    the first slabs wait for the periodic seam, which closes with the last."""
+    box = 1 << 21
+    rng = np.random.default_rng(seed)
+    edges = [box * k // n_slabs for k in range(n_slabs + 1)]
+    order = np.argsort(pos[:, 0], kind="stable")
+    xs = pos[order, 0]
+    cuts = np.searchsorted(xs, edges)
+    slabs = []
+    for k in range(n_slabs):
+        sl = order[cuts[k]:cuts[k + 1]]
+        slabs.append((torch.from_numpy(np.ascontiguousarray(pos[sl])).cuda(),
+                      torch.from_numpy(np.ascontiguousarray(ids[sl]).view(np.int64)).cuda()))
+    params = cso.cso_params_default(meta["u"])
+    out = {}
+    for label, gaps in (("poisson", rng.exponential(mean_gap_s, n_slabs)), ("saturated", np.zeros(n_slabs))):
+        arrivals = np.cumsum(gaps) if label == "poisson" else gaps
+        ctx = cso.Context(local, flags=flags | cso.FLAG_SLOTS(2))
+        bufs, tickets, sched = [], [], []
+        t0 = cso.cso_clock() + 0.01
+        for k in range(n_slabs):
+            sp, si = slabs[k]
+            b = cso.Buffers(sp, si, True, halo_cap=len(sp) // 20 + 64, x_lo=edges[k], x_hi=edges[k + 1],
+                            request_id=1000 + k // n_slabs + (0 if label == "poisson" else 1))
+            target = t0 + arrivals[k]
+            while cso.cso_clock() < target:
+                pass
+            bufs.append(b)
+            sched.append(target)
+            tickets.append(ctx.submit(b, params))
+        for t in tickets:
+            done, rc = ctx.wait(t)
+            assert done and rc == 0, cso.cso_last_error()
+        done_t = np.array([cso.cso_ticket_times(ctx.h, t)[2] for t in tickets])
+        lat = (done_t - np.array(sched)) * 1e3
+        span = done_t.max() - min(sched)
+        out[label] = {"slabs": n_slabs, "particles": int(len(pos)), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "particles_per_s": len(pos) / span,
+                      "arrivals": ("Poisson, mean gap %.0f ms" % (mean_gap_s * 1e3)) if label == "poisson"
+                      else "all at t = 0"}
+        ctx.close()
+    return out
+
+
 def cpu_oracle_rate(samples):
     """Oracle (single thread) on bounded samples of the medium recipe."""
     import oracle as O
@@ -332,7 +379,8 @@ def main():
 
     served = None
     if not args.no_served and ws == 1:
-        served = served_stream(cso, torch, local, flags & ~cso.FLAG_TIMING)
+        served = {"boxes": served_stream(cso, torch, local, flags & ~cso.FLAG_TIMING),
+                  "slab_stream": slab_stream(cso, torch, local, flags & ~cso.FLAG_TIMING, pos, ids, meta)}
 
     if rank != 0:
         if dist is not None:
