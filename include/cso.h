@@ -149,6 +149,14 @@ int cso_params_default(cso_params* p, double l_mean_grid);
 /* Fill the derived block from the primary fields (formulas above). */
 int cso_params_derive(cso_params* p);
 
+/* Scale the thresholds to redshift z of a flat LambdaCDM background with
+ * matter density omega_m0 today (Sec. 2.3.1, Eq. 2, Bryan & Norman 1998):
+ * Delta_L1 = (200 / 18 pi^2)(18 pi^2 + 82 x - 39 x^2) / Omega_m(z) with
+ * x = Omega_m(z) - 1 (mean-relative), Delta_L2 = 4 Delta_L1, delta_L0 =
+ * 60 Delta_L1 / 200, l_fof = 0.25 (Delta_L1 / 200)^(-1/3); b_kernel is kept.
+ * Overwrites those four fields and re-derives. */
+int cso_params_cosmology(cso_params* p, double omega_m0, double z);
+
 /* Run the whole hot path on one periodic box: kernel density, L0, L1, L2,
  * labels and catalogue.  Synchronous: returns after the outputs are written. */
 int cso_find_groups(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out);

@@ -76,6 +76,7 @@ def lib():
         L.orc_derive.argtypes = [P(OrcParams)]
         L.orc_sis_central_density.argtypes = [ctypes.c_double] * 3
         L.orc_sis_central_density.restype = ctypes.c_double
+        L.orc_cosmology.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_void_p]
         L.orc_pred.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_int64]
         L.orc_pred.restype = ctypes.c_int
         L.orc_r_search.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64]
@@ -122,6 +123,13 @@ def _pos(pos):
     pos = np.ascontiguousarray(pos, dtype=np.int32)
     assert pos.ndim == 2 and pos.shape[1] == 3
     return pos
+
+
+def cosmology(omega_m0, z):
+    """(Delta_L0, Delta_L1, Delta_L2, l_FoF) at redshift z."""
+    out = np.zeros(4)
+    lib().orc_cosmology(float(omega_m0), float(z), _ptr(out))
+    return tuple(out.tolist())
 
 
 def pred(n, d, K, u):

@@ -139,6 +139,23 @@ int orc_derive(orc_params* p) {
   return 0;
 }
 
+/* Thresholds at redshift z of a flat LambdaCDM background (Sec. 2.3.1,
+ * Eq. 2): the Bryan & Norman overdensity w.r.t. the critical density,
+ * rescaled from 18 pi^2 to 200 (L1) and 800 (L2), divided by Omega_m(z) to
+ * be relative to the mean; the L0 cut scales with L1 and l_FoF with the
+ * inverse cube root of that change. */
+void orc_cosmology(double omega_m0, double z, double out[4]) {
+  double a3 = pow(1.0 + z, 3.0);
+  double omz = omega_m0 * a3 / (omega_m0 * a3 + 1.0 - omega_m0);
+  double x = omz - 1.0;
+  double crit = 18.0 * M_PI * M_PI + 82.0 * x - 39.0 * x * x;
+  double dl1 = crit * (200.0 / (18.0 * M_PI * M_PI)) / omz;
+  out[0] = 60.0 * dl1 / 200.0;          /* Delta_L0 */
+  out[1] = dl1;                         /* Delta_L1 */
+  out[2] = 4.0 * dl1;                   /* Delta_L2 */
+  out[3] = 0.25 / cbrt(dl1 / 200.0);    /* l_FoF    */
+}
+
 double orc_sis_central_density(double np, double delta, double b) {
   return sis_central_density(np, delta, b);
 }

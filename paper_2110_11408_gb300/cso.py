@@ -110,6 +110,7 @@ def lib(build_if_missing=True):
         L.cso_init.argtypes = [P(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t, ctypes.c_uint32]
         L.cso_params_default.argtypes = [P(CsoParams), ctypes.c_double]
         L.cso_params_derive.argtypes = [P(CsoParams)]
+        L.cso_params_cosmology.argtypes = [P(CsoParams), ctypes.c_double, ctypes.c_double]
         L.cso_find_groups.argtypes = [ctypes.c_void_p, P(CsoInput), P(CsoParams), P(CsoOutput)]
         L.cso_submit.argtypes = [ctypes.c_void_p, P(CsoInput), P(CsoParams), P(CsoOutput), P(ctypes.c_uint64)]
         L.cso_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_int32), ctypes.c_int32]
@@ -164,6 +165,12 @@ def cso_params_default(l_mean_grid, **kw):
     for k, v in kw.items():
         setattr(p, k, v)
     return cso_params_derive(p)
+
+
+def cso_params_cosmology(p, omega_m0, z):
+    """Thresholds and linking length at redshift z (flat LambdaCDM)."""
+    _check(lib().cso_params_cosmology(ctypes.byref(p), float(omega_m0), float(z)), "cso_params_cosmology")
+    return p
 
 
 def cso_params_derive(p):

@@ -85,6 +85,31 @@ extern "C" int cso_params_default(cso_params* p, double l_mean_grid) {
   return cso_params_derive(p);
 }
 
+// Thresholds for a flat LambdaCDM background at redshift z (Sec. 2.3.1,
+// Eq. 2): Delta_base = 18 pi^2 + 82 x - 39 x^2 with x = Omega_m(z) - 1 is the
+// overdensity w.r.t. the critical density; Delta_L1 = (200 / 18 pi^2)
+// Delta_base / Omega_m(z) w.r.t. the mean, Delta_L2 = 4 Delta_L1, and the L0
+// density cut and l_FoF follow the L1 change (the cut in proportion, l_FoF as
+// its inverse cube root); b is unchanged.
+extern "C" int cso_params_cosmology(cso_params* p, double omega_m0, double z) {
+  if (!p || !(omega_m0 > 0 && omega_m0 <= 1) || !(z > -1)) {
+    cso_set_error("invalid cosmology (Omega_m0 = %g, z = %g)", omega_m0, z);
+    return CSO_ERR_ARG;
+  }
+  const double a3 = (1.0 + z) * (1.0 + z) * (1.0 + z);
+  const double om = omega_m0 * a3 / (omega_m0 * a3 + (1.0 - omega_m0));
+  const double x = om - 1.0;
+  const double d18 = 18.0 * M_PI * M_PI;
+  const double base = d18 + 82.0 * x - 39.0 * x * x;
+  const double l1 = 200.0 / d18 * base / om;
+  const double change = l1 / 200.0;
+  p->delta_L1 = l1;
+  p->delta_L2 = 4.0 * l1;
+  p->delta_L0 = 60.0 * change;
+  p->l_fof = 0.25 * pow(change, -1.0 / 3.0);
+  return cso_params_derive(p);
+}
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------

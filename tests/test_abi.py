@@ -59,3 +59,10 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(cso.CsoHalo) == 8 * 19
     assert ctypes.sizeof(cso.CsoInput) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8
     assert ctypes.sizeof(cso.CsoOutput) == 8 * 5 + 8 + 8 + 4 + 4
+
+
+def test_cosmology_scaling_matches_oracle():
+    for om, z in ((0.315, 0.5), (0.3, 0.0), (0.25, 2.0), (1.0, 1.0)):
+        p = cso.cso_params_cosmology(cso.cso_params_default(8192), om, z)
+        ref = O.cosmology(om, z)
+        assert (p.delta_L0, p.delta_L1, p.delta_L2, p.l_fof) == pytest.approx(ref, rel=1e-12)

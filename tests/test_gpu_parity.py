@@ -260,3 +260,13 @@ def test_batched_equals_plain_on_medium_box(ctx, ctx_batched):
     for k in ("sigma", "l0", "l1", "l2"):
         assert np.array_equal(a[k], b[k]), k
     assert np.array_equal(a["halos"], b["halos"])
+
+
+def test_redshift_scaled_thresholds(ctx):
+    """Parity with the thresholds of Table 1's box (z = 0.5, Omega_m = 0.315)."""
+    pos, ids, _ = synth.patch(extent=16.0, lo=-8.0, seed=12)
+    p = cso.cso_params_cosmology(cso.cso_params_default(U64), 0.315, 0.5)
+    po = O.params(U64, delta_L0=p.delta_L0, delta_L1=p.delta_L1, delta_L2=p.delta_L2, l_fof=p.l_fof)
+    g = ctx.find_groups(pos, ids, p)
+    o = O.find_groups(pos, ids, po)
+    assert_same(g, o)

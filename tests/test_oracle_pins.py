@@ -425,3 +425,24 @@ def test_eligibility_radius_controls_satellite_nucleus(two_haloes):
     p95 = O.params(p.u, np_min_L1=1, alpha=(19, 20))
     r95 = O.find_groups(pos, ids, p95)
     assert len(r95["halos"]) < len(r["halos"])
+
+
+# --------------------------------------------------------------------------
+# redshift scaling of the thresholds (Sec. 2.3.1, Eq. 2)
+# --------------------------------------------------------------------------
+
+def test_cosmology_scaling_reproduces_table1():
+    g = GOLD["table1_thresholds_z05"]
+    d0, d1, d2, lf = O.cosmology(g["omega_m0"], g["z"])
+    assert d1 == pytest.approx(g["delta_L1"], rel=1e-3)
+    assert d2 == pytest.approx(g["delta_L2"], rel=1e-3)
+    assert d0 == pytest.approx(g["delta_L0"], rel=1e-3)
+    assert lf == pytest.approx(0.25 * (d1 / 200) ** (-1 / 3), rel=1e-12)
+
+
+def test_cosmology_scaling_einstein_de_sitter_limit():
+    """Omega_m = 1 at all times: x = 0, Delta_base = 18 pi^2, so the
+    Einstein-de Sitter values 60 / 200 / 800 and l_FoF = 0.25 come back."""
+    for z in (0.0, 0.5, 3.0):
+        d0, d1, d2, lf = O.cosmology(1.0, z)
+        assert (d0, d1, d2, lf) == pytest.approx((60.0, 200.0, 800.0, 0.25), rel=1e-12)
