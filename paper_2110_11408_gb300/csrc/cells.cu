@@ -48,15 +48,87 @@ __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_
   return b2 - (d < b2 ? d : b2);  // b2 - d inside the kernel support, else 0
 }
 
-// Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2)
-__global__ void __launch_bounds__(256) k_density(CellGrid g, const int4* __restrict__ spos, int n, uint32_t b2,
-                                                 int include_self, long long* __restrict__ sigma,
-                                                 const uint8_t* __restrict__ only) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n || (only && !only[s])) return;
-  const int4 p = spos[s];
+// Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2).
+//
+// A warp takes 32 consecutive cell-sorted particles.  When all of them sit in
+// one cell (the common case wherever the work is: in dense cells) they share
+// the nine stencil rows, so the warp walks each row once: lanes 0-8 look the
+// rows up, every run is staged into shared memory 32 particles at a time (one
+// coalesced int4 load per lane, the next tile prefetched while the current
+// one is consumed) and each lane sums its own particle against the tile by
+// shared-memory broadcast.  Warps whose particles span several cells walk the
+// stencil lane by lane.
+constexpr int DENS_WARPS = 8;
+
+__global__ void __launch_bounds__(DENS_WARPS * 32) k_density(CellGrid g, const int4* __restrict__ spos, int n,
+                                                            uint32_t b2, int include_self,
+                                                            long long* __restrict__ sigma,
+                                                            const uint8_t* __restrict__ only) {
+  __shared__ int4 tile[DENS_WARPS][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = s < n && (!only || only[s]);
+  const int4 p = s < n ? spos[s] : make_int4(0, 0, 0, 0);
+  const int nc = g.nc;
+  const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc), tc = grid_col(g, p.x);
+  const long long cell = valid ? (long long)grid_cell(g, cz, cy, tc) : -1;
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  if (!vmask) return;
+  const long long cell0 = __shfl_sync(0xffffffffu, cell, __ffs(vmask) - 1);
+  const bool uniform = __all_sync(0xffffffffu, !valid || cell == cell0);
   unsigned long long acc = 0;
-  for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) { acc += kern(spos[t], xq, yq, zq, b2); });
+  if (uniform) {
+    // the cell of the valid lanes (other lanes may hold particles elsewhere)
+    const int src = __ffs(vmask) - 1;
+    const int ccy = __shfl_sync(0xffffffffu, cy, src), ccz = __shfl_sync(0xffffffffu, cz, src);
+    const XCells X = x_cells(g, __shfl_sync(0xffffffffu, tc, src));
+    // lane r < 9: row r = (dz + 1) * 3 + (dy + 1); main run and optional wrapped run
+    uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+    int sy = 0, sz = 0, sx1 = 0;
+    if (lane < 9) {
+      const int zz = wrap_yz(ccz + lane / 3 - 1, nc, sz);
+      const int yy = wrap_yz(ccy + lane % 3 - 1, nc, sy);
+      const uint32_t* row = grid_row(g, zz, yy);
+      lo0 = row[X.a];
+      hi0 = row[X.b + 1];
+      if (X.wl >= 0) { lo1 = row[X.wl]; hi1 = row[X.wl + 1]; sx1 = CSO_BOX; }
+      if (X.wr >= 0) { lo1 = row[X.wr]; hi1 = row[X.wr + 1]; sx1 = -CSO_BOX; }
+    }
+    for (int r = 0; r < 18; ++r) {
+      const int rr = r >> 1;
+      const uint32_t lo = __shfl_sync(0xffffffffu, (r & 1) ? lo1 : lo0, rr);
+      const uint32_t hi = __shfl_sync(0xffffffffu, (r & 1) ? hi1 : hi0, rr);
+      if (lo >= hi) continue;
+      const int xq = p.x + ((r & 1) ? __shfl_sync(0xffffffffu, sx1, rr) : 0);
+      const int yq = p.y + __shfl_sync(0xffffffffu, sy, rr), zq = p.z + __shfl_sync(0xffffffffu, sz, rr);
+      int4 next = lo + lane < hi ? spos[lo + lane] : make_int4(0, 0, 0, 0);
+      for (uint32_t t0 = lo; t0 < hi; t0 += 32) {
+        tile[w][lane] = next;
+        __syncwarp();
+        const uint32_t t1 = t0 + 32;
+        if (t1 + lane < hi) next = spos[t1 + lane];
+        const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
+        // terms are <= b2 <= 2^28: a uint32 partial holds up to 11 of them,
+        // flushed to 64 bits every 8
+        uint32_t part = 0;
+        int k = 0;
+        for (; k + 4 <= m; k += 4) {
+          part += kern(tile[w][k], xq, yq, zq, b2) + kern(tile[w][k + 1], xq, yq, zq, b2) +
+                  kern(tile[w][k + 2], xq, yq, zq, b2) + kern(tile[w][k + 3], xq, yq, zq, b2);
+          if (k & 4) {
+            acc += part;
+            part = 0;
+          }
+        }
+        for (; k < m; ++k) part += kern(tile[w][k], xq, yq, zq, b2);
+        acc += part;
+        __syncwarp();
+      }
+    }
+  } else if (valid) {
+    for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) { acc += kern(spos[t], xq, yq, zq, b2); });
+  }
+  if (!valid) return;
   // the particle met itself once at d = 0
   if (!include_self) acc -= b2;
   sigma[s] = (long long)acc;
@@ -229,13 +301,16 @@ __global__ void k_fof_finish(int* __restrict__ parent, int n, const long long* _
                              unsigned long long* __restrict__ minid) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
-  if (parent[s] < 0) {
-    root[s] = -1;
-    return;
-  }
-  int r = uf_root(parent, s);
+  const int r = parent[s] < 0 ? -1 : uf_root(parent, s);
   root[s] = r;
-  atomicMin(&minid[r], (unsigned long long)sid[s]);
+  // smallest id per root: reduce over the lanes that share a root first
+  const unsigned peers = __match_any_sync(__activemask(), r);
+  unsigned long long v = r >= 0 ? (unsigned long long)sid[s] : ~0ull;
+  for (unsigned m = peers; m; m &= m - 1) {
+    const unsigned long long o = __shfl_sync(peers, v, __ffs(m) - 1);
+    v = o < v ? o : v;
+  }
+  if (r >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(&minid[r], v);
 }
 
 }  // namespace
@@ -285,7 +360,7 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
                   unsigned long long* pairs, cudaStream_t st, const uint8_t* only) {
   if (n <= 0) return CSO_OK;
-  k_density<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, include_self, sigma, only);
+  k_density<<<CL(cdiv(n, DENS_WARPS * 32)), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only);
   if (pairs) k_count_pairs<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, pairs);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;

@@ -175,8 +175,10 @@ __global__ void k_out_l2(const int* __restrict__ ehalo2, int m, const uint32_t* 
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   int h = ehalo2[i];
+  // one atomic per distinct halo in the warp (members of a halo are mostly adjacent)
+  const unsigned peers = __match_any_sync(__activemask(), h);
+  if (h >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h2size[h], (unsigned)__popc(peers));
   if (h < 0) return;
-  atomicAdd(&h2size[h], 1u);
   if (ol2) ol2[spos[gs[ek2[i]]].w] = eid[ek2[hnuc2[h]]];
 }
 
