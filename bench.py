@@ -305,8 +305,13 @@ def main():
     stats = cso.cso_last_stats(cctx.h)
     cctx.close()
 
+    tuned = None
+
     def time_schedule(fl, clk=None):
+        nonlocal tuned
         c = cso.Context(local, flags=fl)
+        if fl & cso.FLAG_BATCHED:  # size bins picked by the autotuner on this machine (untimed)
+            tuned = cso.cso_autotune(c.h, buf, params)
         stream = torch.cuda.ExternalStream(cso.cso_stream(c.h))
         for _ in range(args.warmup):
             cso.cso_find_groups(c.h, buf, params)
@@ -408,7 +413,7 @@ def main():
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "n_particles": n,
-                   "schedule": primary, "l2_flush": "working set > L2 (inputs 336 MB, "
+                   "schedule": primary, "autotuned_bins": tuned, "l2_flush": "working set > L2 (inputs 336 MB, "
                    "cell table 1 GB)", "seed": meta["seed"]},
         "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "served": served, "other_schedule": other,

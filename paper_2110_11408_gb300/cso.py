@@ -110,6 +110,8 @@ def lib(build_if_missing=True):
         L.cso_init.argtypes = [P(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t, ctypes.c_uint32]
         L.cso_params_default.argtypes = [P(CsoParams), ctypes.c_double]
         L.cso_params_derive.argtypes = [P(CsoParams)]
+        L.cso_autotune.argtypes = [ctypes.c_void_p, P(CsoInput), P(CsoParams), P(CsoOutput), P(ctypes.c_int32),
+                                   P(ctypes.c_int32)]
         L.cso_params_cosmology.argtypes = [P(CsoParams), ctypes.c_double, ctypes.c_double]
         L.cso_find_groups.argtypes = [ctypes.c_void_p, P(CsoInput), P(CsoParams), P(CsoOutput)]
         L.cso_submit.argtypes = [ctypes.c_void_p, P(CsoInput), P(CsoParams), P(CsoOutput), P(ctypes.c_uint64)]
@@ -234,6 +236,15 @@ def cso_find_groups(ctx, buffers, params):
     rc = lib().cso_find_groups(ctx, ctypes.byref(buffers.cin), ctypes.byref(params), ctypes.byref(buffers.cout))
     _check(rc, "cso_find_groups")
     return rc
+
+
+def cso_autotune(ctx, buffers, params):
+    """Pick the batched schedule's size bins by timing this request; returns
+    (giant, small)."""
+    g, s = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().cso_autotune(ctx, ctypes.byref(buffers.cin), ctypes.byref(params), ctypes.byref(buffers.cout),
+                              ctypes.byref(g), ctypes.byref(s)), "cso_autotune")
+    return g.value, s.value
 
 
 def cso_submit(ctx, buffers, params):

@@ -208,6 +208,48 @@ int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io) {
 }
 
 // ---------------------------------------------------------------------------
+// autotuner of the batched schedule's size bins
+// ---------------------------------------------------------------------------
+static double level_time(const cso_ctx* c) {
+  double t = 0;
+  for (int i = 0; i < c->nstages; ++i)
+    if (!strcmp(c->stage_name[i], "level1") || !strcmp(c->stage_name[i], "level2")) t += c->stage_ms[i];
+  return t;
+}
+
+extern "C" int cso_autotune(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out,
+                            int32_t* giant, int32_t* small) {
+  if (!c) return CSO_ERR_ARG;
+  static const int giants[] = {4096, 16384, 65536};
+  static const int smalls[] = {32, 64};
+  const uint32_t saved = c->flags;
+  c->flags |= CSO_FLAG_TIMING | CSO_FLAG_BATCHED;
+  LevelSchedule best = c->sched;
+  double best_t = 1e30;
+  int rc = CSO_OK;
+  for (int gi = 0; gi < 3 && rc == CSO_OK; ++gi)
+    for (int si = 0; si < 2 && rc == CSO_OK; ++si) {
+      c->sched.giant = giants[gi];
+      c->sched.small = smalls[si];
+      double t = 1e30;
+      for (int rep = 0; rep < 2 && rc == CSO_OK; ++rep) {
+        rc = cso_find_groups(c, in, p, out);
+        const double lt = level_time(c);
+        if (lt < t) t = lt;
+      }
+      if (rc == CSO_OK && t < best_t) {
+        best_t = t;
+        best = c->sched;
+      }
+    }
+  c->flags = saved;
+  c->sched = best;
+  if (giant) *giant = best.giant;
+  if (small) *small = best.small;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
 // entry points
 // ---------------------------------------------------------------------------
 int check_io(const cso_input* in, const cso_params* p, cso_output* out) {

@@ -257,15 +257,27 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
   const int tc = grid_col(g, p.x);
   const int xcol[3] = {X.a < tc ? X.a : X.wl, tc, X.b > tc ? X.b : X.wr};
   const int xsh[3] = {X.a < tc ? 0 : CSO_BOX, 0, X.b > tc ? 0 : -CSO_BOX};
+  // squared distance from the particle to the near faces of the neighbouring
+  // cells: cells that cannot hold a particle within l_FoF are skipped
+  const int gx = (p.x + g.x0) & (CSO_BOX - 1), gcx = cell_coord(gx, nc);
+  const long long xl = gx - cell_lo(gcx, nc) + 1, xr = cell_lo(gcx + 1, nc) - gx;
+  const long long yl = p.y - cell_lo(cy, nc) + 1, yr = cell_lo(cy + 1, nc) - p.y;
+  const long long zl = p.z - cell_lo(cz, nc) + 1, zr = cell_lo(cz + 1, nc) - p.z;
+  const long long mx[3] = {xl * xl, 0, xr * xr};
+  const long long R2 = lfof2;
   int rs = uf_root(parent, s);
   for (int dz = -1; dz <= 1; ++dz) {
+    const long long mz = dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0);
+    if (mz >= R2) continue;
     int sz;
     const int zz = wrap_yz(cz + dz, nc, sz);
     for (int dy = -1; dy <= 1; ++dy) {
+      const long long my = mz + (dy < 0 ? yl * yl : (dy > 0 ? yr * yr : 0));
+      if (my >= R2) continue;
       int sy;
       const int yy = wrap_yz(cy + dy, nc, sy);
       for (int k = 0; k < 3; ++k) {
-        if (xcol[k] < 0) continue;
+        if (xcol[k] < 0 || my + mx[k] >= R2) continue;
         const int sx = xsh[k];
         const size_t c = grid_cell(g, zz, yy, xcol[k]);
         const int cr = cell_root[c];

@@ -425,7 +425,7 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   L1.cap = stress ? 8 : 2048;
   L1.nb = stress ? 16 : 1024;
   const bool batched = (c->flags & CSO_FLAG_BATCHED) != 0;
-  LevelSchedule sched;
+  const LevelSchedule sched = c->sched;
   unsigned* hcounts = (unsigned*)(c->pinned + 32);
   if (batched) CSO_TRY(level_run_batched(L1, sched, ws, st, c->side, c->fork, c->join, hcounts));
   else CSO_TRY(level_run(L1, st));

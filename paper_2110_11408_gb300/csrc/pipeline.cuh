@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "cells.cuh"
+#include "compaso.cuh"
 
 #define CSO_MAX_STAGES 16
 #define CSO_NSTATS 11
@@ -40,6 +41,8 @@ struct cso_ctx {
   size_t rows_cap = 0;
   uint64_t next_ticket = 0;
   int served_slots = 0;           // worker slots of the served path (0 = 4)
+  LevelSchedule sched;            // size bins of the batched schedule (cso_autotune)
+  double level_ms = 0;            // device time of the last call's CompaSO levels
   ServedState* served = nullptr;  // created by the first cso_submit
 };
 

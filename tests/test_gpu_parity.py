@@ -270,3 +270,15 @@ def test_redshift_scaled_thresholds(ctx):
     g = ctx.find_groups(pos, ids, p)
     o = O.find_groups(pos, ids, po)
     assert_same(g, o)
+
+
+def test_autotuned_schedule_keeps_results(ctx_batched):
+    pos, ids, meta = synth.tiny(seed=5)
+    p, po = both_params(U64)
+    b = cso.Buffers(pos, ids, False)
+    giant, small = cso.cso_autotune(ctx_batched.h, b, p)
+    assert giant in (4096, 16384, 65536) and small in (32, 64)
+    g = ctx_batched.find_groups(pos, ids, p)
+    o = O.find_groups(pos, ids, po)
+    assert_same(g, o)
+    assert_same(b.result(), o)
