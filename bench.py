@@ -261,6 +261,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--bins", default="", help="giant,small size bins of the batched schedule instead of autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -310,8 +311,13 @@ def main():
     def time_schedule(fl, clk=None):
         nonlocal tuned
         c = cso.Context(local, flags=fl)
-        if fl & cso.FLAG_BATCHED:  # size bins picked by the autotuner on this machine (untimed)
-            tuned = cso.cso_autotune(c.h, buf, params)
+        if fl & cso.FLAG_BATCHED:
+            if args.bins:  # fixed size bins (profiling runs)
+                g_, s_ = (int(v) for v in args.bins.split(","))
+                cso.cso_set_schedule(c.h, g_, s_)
+                tuned = (g_, s_)
+            else:  # size bins picked by the autotuner on this machine (untimed)
+                tuned = cso.cso_autotune(c.h, buf, params)
         stream = torch.cuda.ExternalStream(cso.cso_stream(c.h))
         for _ in range(args.warmup):
             cso.cso_find_groups(c.h, buf, params)

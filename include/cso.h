@@ -198,6 +198,10 @@ void cso_free(cso_ctx* ctx);
 int cso_autotune(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out, int32_t* giant,
                  int32_t* small);
 
+/* Set the batched schedule's size bins directly (giant >= 64, 1 <= small
+ * <= 64); the defaults are 16384 and 64. */
+int cso_set_schedule(cso_ctx* ctx, int32_t giant, int32_t small);
+
 /* --- introspection ------------------------------------------------------ */
 
 /* CUDA stream (cudaStream_t) the context issues its work on. */

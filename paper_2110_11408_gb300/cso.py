@@ -247,6 +247,10 @@ def cso_autotune(ctx, buffers, params):
     return g.value, s.value
 
 
+def cso_set_schedule(ctx, giant, small):
+    _check(lib().cso_set_schedule(ctx, int(giant), int(small)), "cso_set_schedule")
+
+
 def cso_submit(ctx, buffers, params):
     t = ctypes.c_uint64()
     rc = lib().cso_submit(ctx, ctypes.byref(buffers.cin), ctypes.byref(params), ctypes.byref(buffers.cout),

@@ -217,6 +217,16 @@ static double level_time(const cso_ctx* c) {
   return t;
 }
 
+extern "C" int cso_set_schedule(cso_ctx* c, int32_t giant, int32_t small) {
+  if (!c || giant < 64 || small < 1 || small > 64) {
+    cso_set_error("size bins need giant >= 64 and 1 <= small <= 64");
+    return CSO_ERR_ARG;
+  }
+  c->sched.giant = giant;
+  c->sched.small = small;
+  return CSO_OK;
+}
+
 extern "C" int cso_autotune(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out,
                             int32_t* giant, int32_t* small) {
   if (!c) return CSO_ERR_ARG;
