@@ -190,24 +190,29 @@ __global__ void k_fof_init(int* __restrict__ parent, int n, const long long* __r
   if (s < n) parent[s] = sigma[s] > T_L0 ? s : -1;
 }
 
-// Sampling round (the idea of Afforest, Sutton et al. 2018): hook every dense
-// particle to the first few linked neighbours in its own cell.  In dense
-// regions this joins almost every cell's dense particles into one tree.
+// First round (in the spirit of Afforest, Sutton et al. 2018): every link
+// inside a cell (each pair once).  Afterwards a cell's dense particles share
+// one tree whenever they are linked within the cell, which is the rule in
+// dense regions, so the full pass can treat such cells as units.
 __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __restrict__ spos, int n,
                                                     uint32_t lfof2, int* __restrict__ parent) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || parent[s] < 0) return;
   const int4 p = spos[s];
   const size_t cell = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
-  int linked = 0;
-  for (uint32_t t = g.start[cell], e = g.start[cell + 1]; t < e && linked < 4; ++t) {
-    if ((int)t == s) continue;
+  int rs = uf_root(parent, s);
+  for (uint32_t t = (uint32_t)s + 1, e = g.start[cell + 1]; t < e; ++t) {
     const int4 q = spos[t];
     const int dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
     const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-    if (d >= lfof2 || parent[t] < 0) continue;
-    uf_unite(parent, s, (int)t);
-    ++linked;
+    if (d >= lfof2) continue;
+    const int pt = parent[t];
+    if (pt < 0 || pt == rs) continue;
+    const int rt = uf_root(parent, pt);
+    if (rt != rs) {
+      uf_unite(parent, rs, rt);
+      rs = uf_root(parent, rs);
+    }
   }
 }
 
@@ -285,8 +290,10 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
         const bool unified = cr >= 0;
         if (unified && uf_root(parent, cr) == rs) continue;
         const int xq = p.x + sx, yq = p.y + sy, zq = p.z + sz;
-        for (uint32_t t = g.start[c], e = g.start[c + 1]; t < e; ++t) {
+        for (uint32_t t = g.start[c], e = g.start[c + 1], it = 0; t < e; ++t, ++it) {
           if (!unified && (int)t <= s) continue;
+          // another thread may have joined the cell to our tree meanwhile
+          if (unified && (it & 15) == 15 && uf_root(parent, cr) == uf_root(parent, rs)) break;
           const int4 q = spos[t];
           const int ddx = xq - q.x, ddy = yq - q.y, ddz = zq - q.z;
           const uint32_t d = (uint32_t)(ddx * ddx) + (uint32_t)(ddy * ddy) + (uint32_t)(ddz * ddz);

@@ -24,6 +24,7 @@ constexpr int LV_THREADS = 256;
 constexpr int NB = 1024;      // histogram bins
 constexpr int CAP = 2048;     // largest bin resolved by an in-block sort
 constexpr int SMALL_N = 2048; // groups sorted whole
+constexpr int COUNT_N = 512;  // groups whose enclosed counts are counted directly
 
 // ---------------------------------------------------------------------------
 // exact predicate n^2 u^6 < K d^3 with K = Km 2^Ke (256-bit integers),
@@ -202,6 +203,41 @@ template <int NT>
 __device__ long long r_search(const int4* __restrict__ epos, long long* __restrict__ ed, int n, int4 pc,
                               const PredConst& c, SelShared& S, const int small_n, const int cap, const int nb) {
   const int tid = threadIdx.x;
+  if (n <= small_n && n <= COUNT_N) {
+    // every member's strictly enclosed count, counted directly: n(<d_i) =
+    // #{j : d_j < d_i}; R^2 is the smallest d_i whose count satisfies the
+    // predicate (2 barriers instead of a sort)
+    for (int j = tid; j < n; j += blockDim.x) {
+      long long d = dist2(pc, epos[j]);
+      ed[j] = d;
+      S.list[j] = d;
+    }
+    if (tid == 0) S.dmax_all = ~0ull;
+    __syncthreads();
+    unsigned long long best = ~0ull, dmax = 0;
+    for (int i = tid; i < n; i += blockDim.x) {
+      const long long di = S.list[i];
+      unsigned cnt = 0;
+      for (int j = 0; j < n; ++j) cnt += S.list[j] < di;
+      if (pred(cnt, (unsigned long long)di, c) && (unsigned long long)di < best) best = (unsigned long long)di;
+      dmax = (unsigned long long)di > dmax ? (unsigned long long)di : dmax;
+    }
+    atomicMin(&S.dmax_all, best);
+    if (tid == 0) S.dmn[0] = 0;
+    __syncthreads();
+    atomicMax(&S.dmn[0], dmax);
+    __syncthreads();
+    long long r = (long long)S.dmax_all;
+    const long long far = (long long)S.dmn[0];
+    __syncthreads();
+    if (S.dmax_all == ~0ull || r < 0) {
+      if (tid == 0) S.list[0] = exhaust_radius((unsigned long long)n, far, c);
+      __syncthreads();
+      r = S.list[0];
+      __syncthreads();
+    }
+    return r;
+  }
   if (n <= small_n) {
     for (int j = tid; j < n; j += blockDim.x) {
       long long d = dist2(pc, epos[j]);
