@@ -42,6 +42,13 @@ __global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* 
   sid[dst] = ids[i];
 }
 
+// min(d, b2) for the squared distance d between the query and q
+__device__ __forceinline__ uint32_t dmin(int4 q, int xq, int yq, int zq, uint32_t b2) {
+  const int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
+  const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+  return d < b2 ? d : b2;
+}
+
 __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_t b2) {
   const int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
   const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
@@ -108,20 +115,23 @@ __global__ void __launch_bounds__(DENS_WARPS * 32) k_density(CellGrid g, const i
         const uint32_t t1 = t0 + 32;
         if (t1 + lane < hi) next = spos[t1 + lane];
         const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
+        // sum of (b2 - min(d, b2)) over the tile = m b2 - sum of min(d, b2);
         // terms are <= b2 <= 2^28: a uint32 partial holds up to 11 of them,
         // flushed to 64 bits every 8
         uint32_t part = 0;
+        unsigned long long mins = 0;
         int k = 0;
         for (; k + 4 <= m; k += 4) {
-          part += kern(tile[w][k], xq, yq, zq, b2) + kern(tile[w][k + 1], xq, yq, zq, b2) +
-                  kern(tile[w][k + 2], xq, yq, zq, b2) + kern(tile[w][k + 3], xq, yq, zq, b2);
+          part += dmin(tile[w][k], xq, yq, zq, b2) + dmin(tile[w][k + 1], xq, yq, zq, b2) +
+                  dmin(tile[w][k + 2], xq, yq, zq, b2) + dmin(tile[w][k + 3], xq, yq, zq, b2);
           if (k & 4) {
-            acc += part;
+            mins += part;
             part = 0;
           }
         }
-        for (; k < m; ++k) part += kern(tile[w][k], xq, yq, zq, b2);
-        acc += part;
+        for (; k < m; ++k) part += dmin(tile[w][k], xq, yq, zq, b2);
+        mins += part;
+        acc += (unsigned long long)m * b2 - mins;
         __syncwarp();
       }
     }
