@@ -104,10 +104,28 @@ def dist_env():
     return ws, rank, local
 
 
+def whole_job_rate(n_per_rank, ms_local, world_size, dist=None, device="cpu"):
+    """Whole-job throughput of a weak-scaling run: every rank processes its
+    own box of n_per_rank particles; the job takes as long as the slowest
+    rank.  Returns (particles/s over all ranks, max ms over ranks)."""
+    ms = float(ms_local)
+    if dist is not None and world_size > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world_size * n_per_rank / (ms / 1e3), ms
+
+
+def make_workload_seed(rank, base=20211022):
+    """Seed of the medium box of one rank (every rank draws its own box)."""
+    return base + 1000 * rank
+
+
 def make_workload(name, seed_offset):
     from paper_2110_11408_gb300 import synth
     if name == "medium":
-        return synth.medium(seed=synth.SEED0 + 1 + 1000 * seed_offset)
+        return synth.medium(seed=make_workload_seed(seed_offset, synth.SEED0 + 1))
     if name == "tiny":
         return synth.tiny(seed=synth.SEED0 + 1000 * seed_offset)
     if name == "medium128":
@@ -341,10 +359,7 @@ def main():
         barrier()
         t = ev0.elapsed_time(ev1) / args.steps
         st = cso.cso_last_stats(c.h)
-        if dist is not None:
-            tt = torch.tensor([t], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        _, t = whole_job_rate(n, t, ws, dist, "cuda")
         return c, t, acc, st
 
     clk = ClockSampler(local)
@@ -380,10 +395,8 @@ def main():
             cso.cso_find_groups(ctx.h, hb, params)
             _ = int(hb.cout.n_halos)
         dt = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        _, ms_e2e = whole_job_rate(n, dt * 1e3, ws, dist, "cuda")
+        dt = ms_e2e / 1e3
         h2d = n * (12 + 8)
         d2h = n * 8 * 4 + int(hb.cout.n_halos) * cso.HALO_DTYPE.itemsize
         e2e = {"value": ws * n / dt, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
