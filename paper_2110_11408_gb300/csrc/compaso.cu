@@ -12,6 +12,7 @@
 //           holds more than 2048 members; small groups are sorted whole;
 //   pass B  tentative membership / competitive reassignment (Eq. 3) and
 //           eligibility marking.
+#include <cooperative_groups.h>
 #include <float.h>
 #include <limits.h>
 
@@ -567,6 +568,339 @@ __global__ void __launch_bounds__(NT) k_level(LevelArgs a, const uint32_t* __res
 }
 
 // ---------------------------------------------------------------------------
+// Giant groups: one thread-block cluster of CS CTAs per group.  CTA r owns
+// the members [r n / CS, (r + 1) n / CS) for the distance, histogram, gather
+// and assignment passes; CTA 0 (the leader) runs the nucleus loop and the
+// select decisions and broadcasts them through its shared memory, which the
+// other CTAs read (and add their histograms into) over DSMEM.  Every CTA
+// passes every cluster barrier, in the same order: all control decisions are
+// read from the leader after a barrier.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+constexpr int CL_CS = 8;      // CTAs per cluster
+constexpr int CL_NT = 1024;   // threads per CTA
+
+enum : int { OP_DONE = 0, OP_HIST = 1, OP_GATHER = 2 };
+
+struct ClusterCtl {
+  int op;
+  int e;                    // next nucleus (member index) or -1
+  int mode;                 // histogram binning of the window
+  int P;                    // members above the stop level
+  long long R2;
+  unsigned long long wlo, whi, base;  // window and members below it
+  unsigned long long lo, hi, cb;      // bin to gather and its enclosed count
+  int from;                 // next bin to examine after a gather
+  int bin;                  // bin being gathered
+  unsigned in_window;
+};
+
+struct ClusterGen {  // the leader's resumable walk over eligible candidates
+  int list[CL_NT];
+  int8_t peak_of[CL_NT];
+  int m, pos, peak_done, c0;
+};
+
+// leader only: the next nucleus in key order (eligible and a local peak), or -1
+__device__ int leader_next_nucleus(const LevelArgs& a, unsigned base, const uint8_t* einel, const uint32_t* egs,
+                                   int P, int glabel, ClusterGen& G, SelShared& S) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  while (true) {
+    if (G.pos >= G.m) {
+      if (G.c0 >= P) return -1;
+      const int j = G.c0 + tid;
+      const unsigned f = (j < P && !einel[j]) ? 1u : 0u;
+      unsigned excl;
+      const unsigned m = block_scan<CL_NT>(f, excl, S.sw);
+      if (f) G.list[excl] = j;
+      __syncthreads();
+      if (tid == 0) {
+        G.m = (int)m;
+        G.pos = 0;
+        G.peak_done = 0;
+        G.c0 += CL_NT;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (G.pos >= G.peak_done) {  // peak flags for the next 32 candidates, a warp each
+      const int k = G.pos + warp;
+      if (k < G.m) {
+        const int e = G.list[k];
+        const bool ok = !einel[e] && warp_is_peak(a, egs[e], glabel);
+        if (lane == 0) G.peak_of[k] = ok;
+      }
+      __syncthreads();
+      if (tid == 0) G.peak_done = min(G.pos + CL_NT / 32, G.m);
+      __syncthreads();
+    }
+    const int k = G.pos;
+    const int e = G.list[k];
+    const bool take = G.peak_of[k] && !einel[e];  // eligibility may have changed since the scan
+    __syncthreads();
+    if (tid == 0) G.pos = k + 1;
+    __syncthreads();
+    if (take) return e;
+  }
+}
+
+// leader only: decide the next step of the select from bin `from` of the
+// merged histogram (S.cnt / S.dmn / S.dmx / S.clo, window in Ctl)
+__device__ void leader_decide(ClusterCtl& C, SelShared& S, int from, int nb, int cap, int n, const PredConst& c) {
+  const int tid = threadIdx.x;
+  if (tid == 0) S.best = NB;
+  __syncthreads();
+  for (int b = from + tid; b < NB; b += blockDim.x)
+    if (S.cnt[b] && pred(C.base + S.clo[b], S.dmx[b], c)) atomicMin(&S.best, b);
+  __syncthreads();
+  if (tid == 0) {
+    const int b = S.best;
+    if (b < NB) {
+      const unsigned long long lo = S.dmn[b], hi = S.dmx[b], cb = C.base + S.clo[b];
+      if (lo == hi) {  // one distinct value: the bin test was the exact predicate
+        C.op = OP_DONE;
+        C.R2 = (long long)lo;
+      } else if (S.cnt[b] <= (unsigned)cap) {
+        C.op = OP_GATHER;
+        C.lo = lo;
+        C.hi = hi;
+        C.cb = cb;
+        C.bin = b;
+        S.nlist = 0;
+      } else {  // narrow the window to the bin
+        C.op = OP_HIST;
+        C.wlo = lo;
+        C.whi = hi;
+        C.base = cb;
+        C.mode = 1;
+      }
+    } else {  // nothing in the window: move past it
+      C.base += C.in_window;
+      if (C.whi >= S.dmax_all) {
+        C.op = OP_DONE;
+        C.R2 = exhaust_radius((unsigned long long)n, (long long)S.dmax_all, c);
+      } else {
+        C.op = OP_HIST;
+        C.wlo = C.whi + 1;
+        C.whi = S.dmax_all;
+        C.mode = 1;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// R^2 of nucleus pc over the group, computed by the whole cluster
+__device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __restrict__ epos,
+                                      long long* __restrict__ ed, int n, int lo_r, int hi_r, int4 pc,
+                                      const PredConst& c, SelShared& S, ClusterCtl& C, int cap, int nb) {
+  const int tid = threadIdx.x;
+  const bool leader = cluster.block_rank() == 0;
+  SelShared* LS = cluster.map_shared_rank(&S, 0);
+  ClusterCtl* LC = cluster.map_shared_rank(&C, 0);
+  const float scale0 = c.bin_scale0 / (float)((n + nb - 2) / (nb - 1));
+  // the first pass: threshold-count bins over every distance
+  unsigned long long wlo = 0, whi = ~0ull;
+  int mode = 0;
+  bool first = true;
+  if (leader && tid == 0) {
+    C.base = 0;
+    C.wlo = 0;
+    C.whi = ~0ull;
+    C.mode = 0;
+  }
+  int op = OP_HIST;
+  while (true) {
+    if (op == OP_HIST) {
+      for (int b = tid; b < NB; b += blockDim.x) {
+        S.cnt[b] = 0;
+        S.dmn[b] = ~0ull;
+        S.dmx[b] = 0;
+      }
+      if (tid == 0 && first) S.dmax_all = 0;
+      __syncthreads();
+      const unsigned long long span = whi - wlo + 1;
+      for (int j = lo_r + tid; j < hi_r; j += blockDim.x) {
+        unsigned long long d;
+        if (first) {
+          d = (unsigned long long)dist2(pc, epos[j]);
+          ed[j] = (long long)d;
+          atomicMax(&S.dmax_all, d);
+        } else {
+          d = (unsigned long long)ed[j];
+        }
+        if (d < wlo || d > whi) continue;
+        int b;
+        if (mode == 0) {
+          const float f = (float)d;
+          const float g = f * sqrtf(f) * scale0;
+          b = g < (float)(nb - 1) ? (int)g : nb - 1;
+        } else {
+          b = (int)(((d - wlo) * (unsigned long long)nb) / span);
+        }
+        atomicAdd(&S.cnt[b], 1u);
+        atomicMin(&S.dmn[b], d);
+        atomicMax(&S.dmx[b], d);
+      }
+      __syncthreads();
+      cluster.sync();  // every CTA's local histogram is complete; the leader's is its own share
+      if (!leader) {
+        for (int b = tid; b < NB; b += blockDim.x)
+          if (S.cnt[b]) {
+            atomicAdd(&LS->cnt[b], S.cnt[b]);
+            atomicMin(&LS->dmn[b], S.dmn[b]);
+            atomicMax(&LS->dmx[b], S.dmx[b]);
+          }
+        if (first && tid == 0) atomicMax(&LS->dmax_all, S.dmax_all);
+      }
+      first = false;
+      cluster.sync();  // merged
+      if (leader) {
+        constexpr int per = NB / CL_NT;
+        unsigned loc[per > 0 ? per : 1];
+        unsigned sum = 0;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+          loc[q] = S.cnt[tid * per + q];
+          sum += loc[q];
+        }
+        unsigned excl;
+        const unsigned tot = block_scan<CL_NT>(sum, excl, S.sw);
+        unsigned run = excl;
+#pragma unroll
+        for (int q = 0; q < per; ++q) {
+          S.clo[tid * per + q] = run;
+          run += loc[q];
+        }
+        if (tid == 0) C.in_window = tot;
+        __syncthreads();
+        leader_decide(C, S, 0, nb, cap, n, c);
+      }
+    } else {  // OP_GATHER: every CTA appends its members of the bin to the leader's list
+      const unsigned long long glo = LC->lo, ghi = LC->hi;
+      for (int j = lo_r + tid; j < hi_r; j += blockDim.x) {
+        const unsigned long long d = (unsigned long long)ed[j];
+        if (d >= glo && d <= ghi) LS->list[atomicAdd(&LS->nlist, 1)] = (long long)d;
+      }
+      cluster.sync();  // the list is complete
+      if (leader) {
+        const int m = S.nlist;
+        const int p2 = pow2_at_least(m);
+        for (int j = m + tid; j < p2; j += blockDim.x) S.list[j] = LLONG_MAX;
+        __syncthreads();
+        bitonic_sort(S.list, p2);
+        const int k = scan_sorted(S.list, m, C.cb, c, &S.best);
+        if (k < m) {
+          if (tid == 0) {
+            C.op = OP_DONE;
+            C.R2 = S.list[k];
+          }
+          __syncthreads();
+        } else {
+          leader_decide(C, S, C.bin + 1, nb, cap, n, c);
+        }
+      }
+    }
+    cluster.sync();  // the leader's decision is published
+    op = LC->op;
+    if (op == OP_DONE) break;
+    wlo = LC->wlo;
+    whi = LC->whi;
+    mode = LC->mode;
+    cluster.sync();  // everyone has read it before the leader writes the next one
+  }
+  const long long R2 = LC->R2;
+  cluster.sync();
+  return R2;
+}
+
+__global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
+    k_level_cluster(LevelArgs a, const uint32_t* __restrict__ segs) {
+  __shared__ SelShared S;
+  __shared__ ClusterCtl C;
+  __shared__ ClusterGen G;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const bool leader = rank == 0;
+  const int seg = (int)segs[blockIdx.x / CL_CS];
+  const unsigned base = a.seg_off[seg];
+  const int n = (int)(a.seg_off[seg + 1] - base);
+  const int tid = threadIdx.x;
+  const int lo_r = (int)((long long)n * rank / CL_CS), hi_r = (int)((long long)n * (rank + 1) / CL_CS);
+  const int4* epos = a.epos + base;
+  const long long* esig = a.esig + base;
+  const uint32_t* egs = a.egs + base;
+  int* eslot = a.eslot + base;
+  long long* edold = a.edold + base;
+  uint8_t* einel = a.einel + base;
+  long long* ed = a.ed + base;
+  ClusterCtl* LC = cluster.map_shared_rank(&C, 0);
+
+  for (int j = lo_r + tid; j < hi_r; j += blockDim.x) {
+    eslot[j] = -1;
+    einel[j] = 0;
+  }
+  if (leader && tid == 0) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (esig[mid] > a.T_min) lo = mid + 1;
+      else hi = mid;
+    }
+    C.P = lo;
+    G.m = 0;
+    G.pos = 0;
+    G.peak_done = 0;
+    G.c0 = 0;
+  }
+  const int glabel = a.slab[egs[0]];
+  const long long anum2 = (long long)a.alpha_num * a.alpha_num, aden2 = (long long)a.alpha_den * a.alpha_den;
+  cluster.sync();  // slots and flags initialised everywhere
+  int nn = 0;
+  while (true) {
+    if (leader) {
+      __syncthreads();
+      const int e = leader_next_nucleus(a, base, einel, egs, C.P, glabel, G, S);
+      if (tid == 0) C.e = e;
+    }
+    cluster.sync();
+    const int e = LC->e;
+    if (e < 0) break;
+    const int4 pc = epos[e];
+    const long long R2 = cluster_r_search(cluster, epos, ed, n, lo_r, hi_r, pc, a.pc, S, C, a.cap, a.nb);
+    // steps 1 and 3 on this CTA's share of the members
+    for (int j = lo_r + tid; j < hi_r; j += blockDim.x) {
+      const long long d = ed[j];
+      if (d >= R2) continue;
+      const int sl = eslot[j];
+      bool take;
+      if (sl < 0) {
+        take = true;
+      } else {
+        const long long R2old = a.nuc_R2[base + sl];
+        take = (__int128)R2 * edold[j] * a.roche_den >= (__int128)a.roche_num * R2old * d;
+      }
+      if (take) {
+        eslot[j] = nn;
+        edold[j] = d;
+      }
+      if ((__int128)aden2 * d < (__int128)anum2 * R2) einel[j] = 1;
+    }
+    if (leader && tid == 0) {
+      a.nuc_member[base + nn] = (uint32_t)e;
+      a.nuc_R2[base + nn] = R2;
+    }
+    ++nn;
+    cluster.sync();  // assignments and eligibility visible to the leader's next walk
+  }
+  if (leader && tid == 0) {
+    a.nnuc[seg] = (uint32_t)nn;
+    if (a.work && nn) atomicAdd(a.work, (unsigned long long)nn * (unsigned long long)n);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // One small group (n <= 64 members) per warp.  Members live in registers
 // (lane l holds members l and l + 32).  The enclosed count n(<d_i) of every
 // member is counted directly over all members (n^2 compares), so R^2 =
@@ -750,7 +1084,7 @@ int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws
   if (ng > 0) {
     CSO_CUDA(cudaEventRecord(fork, st));
     CSO_CUDA(cudaStreamWaitEvent(side, fork, 0));
-    k_level<1024><<<CL(ng), 1024, 0, side>>>(a, pv);
+    k_level_cluster<<<CL(ng * CL_CS), CL_NT, 0, side>>>(a, pv);
     CSO_CUDA(cudaGetLastError());
   }
   if (nm > 0) k_level<256><<<CL(nm), 256, 0, st>>>(a, pv + ng);

@@ -282,3 +282,28 @@ def test_autotuned_schedule_keeps_results(ctx_batched):
     o = O.find_groups(pos, ids, po)
     assert_same(g, o)
     assert_same(b.result(), o)
+
+
+def test_cluster_path_for_every_group_above_64():
+    """Giant threshold 64: every group above 64 members runs on an 8-CTA
+    thread-block cluster (DSMEM histogram merge, leader-driven select)."""
+    c = cso.Context(0, flags=cso.FLAG_BATCHED)
+    try:
+        cso.cso_set_schedule(c.h, 64, 64)
+        pos, ids, meta = synth.tiny()
+        g, o = run_both(c, pos, ids)
+        assert_same(g, o)
+    finally:
+        c.close()
+
+
+def test_cluster_path_select_stress():
+    c = cso.Context(0, flags=cso.FLAG_BATCHED | cso.FLAG_SELECT_STRESS)
+    try:
+        cso.cso_set_schedule(c.h, 64, 8)
+        for seed in (4, 6):
+            pos, ids, _ = synth.patch(extent=18.0, lo=-3.0, seed=seed, nmax=4000)
+            g, o = run_both(c, pos, ids)
+            assert_same(g, o)
+    finally:
+        c.close()
