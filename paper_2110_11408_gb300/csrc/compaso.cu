@@ -898,6 +898,9 @@ __global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
     a.nnuc[seg] = (uint32_t)nn;
     if (a.work && nn) atomicAdd(a.work, (unsigned long long)nn * (unsigned long long)n);
   }
+  // no CTA may exit while another can still read its shared memory (the last
+  // read of the leader's C.e happens after the final barrier of the loop)
+  cluster.sync();
 }
 
 // ---------------------------------------------------------------------------
