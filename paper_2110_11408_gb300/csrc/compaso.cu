@@ -667,7 +667,6 @@ __device__ void leader_decide(ClusterCtl& C, SelShared& S, int from, int nb, int
         C.hi = hi;
         C.cb = cb;
         C.bin = b;
-        S.nlist = 0;
       } else {  // narrow the window to the bin
         C.op = OP_HIST;
         C.wlo = lo;
@@ -691,13 +690,15 @@ __device__ void leader_decide(ClusterCtl& C, SelShared& S, int from, int nb, int
   __syncthreads();
 }
 
-// R^2 of nucleus pc over the group, computed by the whole cluster
+// R^2 of nucleus pc over the group, computed by the whole cluster.  Every CTA
+// builds its histogram (and, for a gather, its list) in its own shared
+// memory; after the barrier the leader reads the others' with plain DSMEM
+// loads and combines them.
 __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __restrict__ epos,
                                       long long* __restrict__ ed, int n, int lo_r, int hi_r, int4 pc,
                                       const PredConst& c, SelShared& S, ClusterCtl& C, int cap, int nb) {
   const int tid = threadIdx.x;
   const bool leader = cluster.block_rank() == 0;
-  SelShared* LS = cluster.map_shared_rank(&S, 0);
   ClusterCtl* LC = cluster.map_shared_rank(&C, 0);
   const float scale0 = c.bin_scale0 / (float)((n + nb - 2) / (nb - 1));
   // the first pass: threshold-count bins over every distance
@@ -744,19 +745,32 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
         atomicMax(&S.dmx[b], d);
       }
       __syncthreads();
-      cluster.sync();  // every CTA's local histogram is complete; the leader's is its own share
-      if (!leader) {
-        for (int b = tid; b < NB; b += blockDim.x)
-          if (S.cnt[b]) {
-            atomicAdd(&LS->cnt[b], S.cnt[b]);
-            atomicMin(&LS->dmn[b], S.dmn[b]);
-            atomicMax(&LS->dmx[b], S.dmx[b]);
-          }
-        if (first && tid == 0) atomicMax(&LS->dmax_all, S.dmax_all);
-      }
-      first = false;
-      cluster.sync();  // merged
+      cluster.sync();  // every CTA's histogram of its members is complete
       if (leader) {
+        // combine the CTAs' histograms (the leader's own is the first share)
+        for (int b = tid; b < NB; b += blockDim.x) {
+          unsigned cn = S.cnt[b];
+          unsigned long long mn = S.dmn[b], mx = S.dmx[b];
+          for (int r = 1; r < CL_CS; ++r) {
+            const SelShared* R = cluster.map_shared_rank(&S, r);
+            cn += R->cnt[b];
+            const unsigned long long a1 = R->dmn[b], a2 = R->dmx[b];
+            mn = a1 < mn ? a1 : mn;
+            mx = a2 > mx ? a2 : mx;
+          }
+          S.cnt[b] = cn;
+          S.dmn[b] = mn;
+          S.dmx[b] = mx;
+        }
+        if (first && tid == 0) {
+          unsigned long long m = S.dmax_all;
+          for (int r = 1; r < CL_CS; ++r) {
+            const unsigned long long v = cluster.map_shared_rank(&S, r)->dmax_all;
+            m = v > m ? v : m;
+          }
+          S.dmax_all = m;
+        }
+        __syncthreads();
         constexpr int per = NB / CL_NT;
         unsigned loc[per > 0 ? per : 1];
         unsigned sum = 0;
@@ -777,15 +791,27 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
         __syncthreads();
         leader_decide(C, S, 0, nb, cap, n, c);
       }
-    } else {  // OP_GATHER: every CTA appends its members of the bin to the leader's list
+      first = false;
+    } else {  // OP_GATHER: every CTA lists its members of the bin, the leader collects them
       const unsigned long long glo = LC->lo, ghi = LC->hi;
+      if (tid == 0) S.nlist = 0;
+      __syncthreads();
       for (int j = lo_r + tid; j < hi_r; j += blockDim.x) {
         const unsigned long long d = (unsigned long long)ed[j];
-        if (d >= glo && d <= ghi) LS->list[atomicAdd(&LS->nlist, 1)] = (long long)d;
+        if (d >= glo && d <= ghi) S.list[atomicAdd(&S.nlist, 1)] = (long long)d;
       }
-      cluster.sync();  // the list is complete
+      __syncthreads();
+      cluster.sync();  // every CTA's list is complete
       if (leader) {
-        const int m = S.nlist;
+        int off = S.nlist;
+        for (int r = 1; r < CL_CS; ++r) {
+          const SelShared* R = cluster.map_shared_rank(&S, r);
+          const int mr = R->nlist;
+          for (int j = tid; j < mr; j += blockDim.x) S.list[off + j] = R->list[j];
+          off += mr;
+        }
+        __syncthreads();
+        const int m = off;
         const int p2 = pow2_at_least(m);
         for (int j = m + tid; j < p2; j += blockDim.x) S.list[j] = LLONG_MAX;
         __syncthreads();
@@ -802,7 +828,7 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
         }
       }
     }
-    cluster.sync();  // the leader's decision is published
+    cluster.sync();  // the leader's decision is published (and it has read everyone's shares)
     op = LC->op;
     if (op == OP_DONE) break;
     wlo = LC->wlo;
