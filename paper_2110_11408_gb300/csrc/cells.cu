@@ -65,71 +65,176 @@ __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_
 // one is consumed) and each lane sums its own particle against the tile by
 // shared-memory broadcast.  Warps whose particles span several cells walk the
 // stencil lane by lane.
+//
+// In the shared walk, offsets are taken from the warp's first particle o:
+// the query is q = p - o, a staged neighbour c = t - shift - o, and
+// d = |q|^2 + |c|^2 - 2 q.c.  The lane that stages c also stores |c|^2, so a
+// pair costs three multiply-adds, one add and one min.  The arithmetic is
+// modulo 2^32: every component of q - c is below 2 cells = 2^15 units, so the
+// true d is below 3 * 2^30 and the wrapped result is exact.
+//
+// Blocks run heaviest first: a cost pass estimates each block's pair count,
+// files the block under floor(log2(cost)) and the density launch takes block
+// order[blockIdx.x], so the dense-halo blocks start in the first wave instead
+// of forming the tail.
 constexpr int DENS_WARPS = 8;
+constexpr int DENS_CLASSES = 33;
+
+__device__ __forceinline__ uint32_t sq3(int x, int y, int z) {
+  return (uint32_t)x * (uint32_t)x + (uint32_t)y * (uint32_t)y + (uint32_t)z * (uint32_t)z;
+}
+
+// min(d, b2) for the staged neighbour c = (offset, |offset|^2) and the query
+// with P = |q|^2 and a = -2 q
+__device__ __forceinline__ uint32_t dmin_dot(int4 c, uint32_t P, uint32_t ax, uint32_t ay, uint32_t az, uint32_t b2) {
+  const uint32_t d = (uint32_t)c.w + P + ax * (uint32_t)c.x + ay * (uint32_t)c.y + az * (uint32_t)c.z;
+  return d < b2 ? d : b2;
+}
+
+// The shared-walk setup of one warp: whether its valid particles share a
+// cell and, for lanes 0-8, the runs of stencil row (dz + 1) * 3 + (dy + 1):
+// main run [lo0, hi0) and the wrapped run [lo1, hi1) with its x shift sx1.
+struct WarpRows {
+  bool uniform;
+  int src;  // first valid lane
+  uint32_t lo0, hi0, lo1, hi1;
+  int sy, sz, sx1;
+};
+
+__device__ __forceinline__ WarpRows warp_rows(const CellGrid& g, int4 p, bool valid, unsigned vmask, int lane) {
+  WarpRows R{};
+  const int nc = g.nc;
+  const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc), tc = grid_col(g, p.x);
+  const long long cell = valid ? (long long)grid_cell(g, cz, cy, tc) : -1;
+  R.src = __ffs(vmask) - 1;
+  const long long cell0 = __shfl_sync(0xffffffffu, cell, R.src);
+  R.uniform = __all_sync(0xffffffffu, !valid || cell == cell0);
+  if (!R.uniform) return R;
+  const int ccy = __shfl_sync(0xffffffffu, cy, R.src), ccz = __shfl_sync(0xffffffffu, cz, R.src);
+  const XCells X = x_cells(g, __shfl_sync(0xffffffffu, tc, R.src));
+  if (lane < 9) {
+    const int zz = wrap_yz(ccz + lane / 3 - 1, nc, R.sz);
+    const int yy = wrap_yz(ccy + lane % 3 - 1, nc, R.sy);
+    const uint32_t* row = grid_row(g, zz, yy);
+    R.lo0 = row[X.a];
+    R.hi0 = row[X.b + 1];
+    if (X.wl >= 0) { R.lo1 = row[X.wl]; R.hi1 = row[X.wl + 1]; R.sx1 = CSO_BOX; }
+    if (X.wr >= 0) { R.lo1 = row[X.wr]; R.hi1 = row[X.wr + 1]; R.sx1 = -CSO_BOX; }
+  }
+  return R;
+}
+
+// cost class and in-class rank of every density block
+__global__ void __launch_bounds__(DENS_WARPS * 32) k_density_cost(CellGrid g, const int4* __restrict__ spos, int n,
+                                                                 const uint8_t* __restrict__ only,
+                                                                 uint8_t* __restrict__ cls,
+                                                                 uint32_t* __restrict__ rank,
+                                                                 uint32_t* __restrict__ counts) {
+  __shared__ unsigned long long bcost;
+  if (threadIdx.x == 0) bcost = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = s < n && (!only || only[s]);
+  const int4 p = s < n ? spos[s] : make_int4(0, 0, 0, 0);
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  if (vmask) {
+    const WarpRows R = warp_rows(g, p, valid, vmask, lane);
+    unsigned long long c;
+    if (R.uniform) {
+      // candidates the shared walk streams
+      c = __reduce_add_sync(0xffffffffu, (R.hi0 - R.lo0) + (R.hi1 - R.lo1));
+    } else {
+      // lane walks diverge: charge the fullest own cell 27 times
+      uint32_t m = 0;
+      if (valid) {
+        const size_t k = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
+        m = g.start[k + 1] - g.start[k];
+      }
+      c = 27ull * __reduce_max_sync(0xffffffffu, m);
+    }
+    if (lane == 0) atomicAdd(&bcost, c);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long c = bcost | 1ull;
+    const int k = 63 - __clzll(c);
+    const int kc = k < DENS_CLASSES - 1 ? k : DENS_CLASSES - 1;
+    cls[blockIdx.x] = (uint8_t)kc;
+    rank[blockIdx.x] = atomicAdd(&counts[kc], 1u);
+  }
+}
+
+// order[position] = block, classes in decreasing cost
+__global__ void k_density_order(const uint8_t* __restrict__ cls, const uint32_t* __restrict__ rank,
+                                const uint32_t* __restrict__ counts, int nb, uint32_t* __restrict__ order) {
+  __shared__ uint32_t first[DENS_CLASSES];
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int k = DENS_CLASSES - 1; k >= 0; --k) {
+      first[k] = acc;
+      acc += counts[k];
+    }
+  }
+  __syncthreads();
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < nb) order[first[cls[b]] + rank[b]] = (uint32_t)b;
+}
 
 __global__ void __launch_bounds__(DENS_WARPS * 32) k_density(CellGrid g, const int4* __restrict__ spos, int n,
                                                             uint32_t b2, int include_self,
                                                             long long* __restrict__ sigma,
-                                                            const uint8_t* __restrict__ only) {
+                                                            const uint8_t* __restrict__ only,
+                                                            const uint32_t* __restrict__ order) {
   __shared__ int4 tile[DENS_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int blk = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
+  const int s = blk * blockDim.x + threadIdx.x;
   const bool valid = s < n && (!only || only[s]);
   const int4 p = s < n ? spos[s] : make_int4(0, 0, 0, 0);
-  const int nc = g.nc;
-  const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc), tc = grid_col(g, p.x);
-  const long long cell = valid ? (long long)grid_cell(g, cz, cy, tc) : -1;
   const unsigned vmask = __ballot_sync(0xffffffffu, valid);
   if (!vmask) return;
-  const long long cell0 = __shfl_sync(0xffffffffu, cell, __ffs(vmask) - 1);
-  const bool uniform = __all_sync(0xffffffffu, !valid || cell == cell0);
+  const WarpRows R = warp_rows(g, p, valid, vmask, lane);
   unsigned long long acc = 0;
-  if (uniform) {
-    // the cell of the valid lanes (other lanes may hold particles elsewhere)
-    const int src = __ffs(vmask) - 1;
-    const int ccy = __shfl_sync(0xffffffffu, cy, src), ccz = __shfl_sync(0xffffffffu, cz, src);
-    const XCells X = x_cells(g, __shfl_sync(0xffffffffu, tc, src));
-    // lane r < 9: row r = (dz + 1) * 3 + (dy + 1); main run and optional wrapped run
-    uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-    int sy = 0, sz = 0, sx1 = 0;
-    if (lane < 9) {
-      const int zz = wrap_yz(ccz + lane / 3 - 1, nc, sz);
-      const int yy = wrap_yz(ccy + lane % 3 - 1, nc, sy);
-      const uint32_t* row = grid_row(g, zz, yy);
-      lo0 = row[X.a];
-      hi0 = row[X.b + 1];
-      if (X.wl >= 0) { lo1 = row[X.wl]; hi1 = row[X.wl + 1]; sx1 = CSO_BOX; }
-      if (X.wr >= 0) { lo1 = row[X.wr]; hi1 = row[X.wr + 1]; sx1 = -CSO_BOX; }
-    }
+  if (R.uniform) {
+    const int ox = __shfl_sync(0xffffffffu, p.x, R.src), oy = __shfl_sync(0xffffffffu, p.y, R.src),
+              oz = __shfl_sync(0xffffffffu, p.z, R.src);
+    const int qx = p.x - ox, qy = p.y - oy, qz = p.z - oz;
+    const uint32_t P = sq3(qx, qy, qz);
+    const uint32_t ax = (uint32_t)(-2 * qx), ay = (uint32_t)(-2 * qy), az = (uint32_t)(-2 * qz);
     for (int r = 0; r < 18; ++r) {
       const int rr = r >> 1;
-      const uint32_t lo = __shfl_sync(0xffffffffu, (r & 1) ? lo1 : lo0, rr);
-      const uint32_t hi = __shfl_sync(0xffffffffu, (r & 1) ? hi1 : hi0, rr);
+      const uint32_t lo = __shfl_sync(0xffffffffu, (r & 1) ? R.lo1 : R.lo0, rr);
+      const uint32_t hi = __shfl_sync(0xffffffffu, (r & 1) ? R.hi1 : R.hi0, rr);
       if (lo >= hi) continue;
-      const int xq = p.x + ((r & 1) ? __shfl_sync(0xffffffffu, sx1, rr) : 0);
-      const int yq = p.y + __shfl_sync(0xffffffffu, sy, rr), zq = p.z + __shfl_sync(0xffffffffu, sz, rr);
+      // the neighbour's image nearest the warp: t - shift
+      const int bx = ox + ((r & 1) ? __shfl_sync(0xffffffffu, R.sx1, rr) : 0);
+      const int by = oy + __shfl_sync(0xffffffffu, R.sy, rr), bz = oz + __shfl_sync(0xffffffffu, R.sz, rr);
       int4 next = lo + lane < hi ? spos[lo + lane] : make_int4(0, 0, 0, 0);
       for (uint32_t t0 = lo; t0 < hi; t0 += 32) {
-        tile[w][lane] = next;
+        {
+          const int cx = next.x - bx, cy = next.y - by, cz = next.z - bz;
+          tile[w][lane] = make_int4(cx, cy, cz, (int)sq3(cx, cy, cz));
+        }
         __syncwarp();
         const uint32_t t1 = t0 + 32;
         if (t1 + lane < hi) next = spos[t1 + lane];
         const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
         // sum of (b2 - min(d, b2)) over the tile = m b2 - sum of min(d, b2);
-        // terms are <= b2 <= 2^28: a uint32 partial holds up to 11 of them,
+        // terms are <= b2 <= 2^28: a uint32 partial holds up to 15 of them,
         // flushed to 64 bits every 8
         uint32_t part = 0;
         unsigned long long mins = 0;
         int k = 0;
         for (; k + 4 <= m; k += 4) {
-          part += dmin(tile[w][k], xq, yq, zq, b2) + dmin(tile[w][k + 1], xq, yq, zq, b2) +
-                  dmin(tile[w][k + 2], xq, yq, zq, b2) + dmin(tile[w][k + 3], xq, yq, zq, b2);
+          part += dmin_dot(tile[w][k], P, ax, ay, az, b2) + dmin_dot(tile[w][k + 1], P, ax, ay, az, b2) +
+                  dmin_dot(tile[w][k + 2], P, ax, ay, az, b2) + dmin_dot(tile[w][k + 3], P, ax, ay, az, b2);
           if (k & 4) {
             mins += part;
             part = 0;
           }
         }
-        for (; k < m; ++k) part += dmin(tile[w][k], xq, yq, zq, b2);
+        for (; k < m; ++k) part += dmin_dot(tile[w][k], P, ax, ay, az, b2);
         mins += part;
         acc += (unsigned long long)m * b2 - mins;
         __syncwarp();
@@ -387,11 +492,25 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
 }
 
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
-                  unsigned long long* pairs, cudaStream_t st, const uint8_t* only) {
+                  unsigned long long* pairs, Workspace& ws, cudaStream_t st, const uint8_t* only) {
   if (n <= 0) return CSO_OK;
-  k_density<<<CL(cdiv(n, DENS_WARPS * 32)), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only);
+  const int nb = cdiv(n, DENS_WARPS * 32);
+  const size_t mark = ws.off;
+  uint32_t* order = ws.get<uint32_t>(nb);
+  uint32_t* rank = ws.get<uint32_t>(nb);
+  uint32_t* counts = ws.get<uint32_t>(DENS_CLASSES);
+  uint8_t* cls = ws.get<uint8_t>(nb);
+  if (!order || !rank || !counts || !cls) {
+    cso_set_error("workspace exhausted in the density pass");
+    return CSO_ERR_BUDGET;
+  }
+  CSO_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * DENS_CLASSES, st));
+  k_density_cost<<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, only, cls, rank, counts);
+  k_density_order<<<CL(cdiv(nb, 256)), 256, 0, st>>>(cls, rank, counts, nb, order);
+  k_density<<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only, order);
   if (pairs) k_count_pairs<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, pairs);
   CSO_CUDA(cudaGetLastError());
+  ws.off = mark;
   return CSO_OK;
 }
 

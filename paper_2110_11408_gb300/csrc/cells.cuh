@@ -114,7 +114,7 @@ int cells_choose(long long b2, int* nc_out);
 int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGrid& g, uint32_t* start,
               int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st);
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
-                  unsigned long long* pairs, cudaStream_t st, const uint8_t* only = nullptr);
+                  unsigned long long* pairs, Workspace& ws, cudaStream_t st, const uint8_t* only = nullptr);
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
               const uint64_t* sid, int* parent, int* root, unsigned long long* minid, int* cell_root,
               cudaStream_t st);

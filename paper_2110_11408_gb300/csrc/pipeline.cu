@@ -617,7 +617,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   ALLOC(long long, sigma, n);
   const bool count_pairs = (c->flags & CSO_FLAG_COUNT_PAIRS) != 0;
   CSO_TRY(cells_density(g, spos, N, (uint32_t)p->b2, p->include_self, sigma, count_pairs ? &meta->pairs : nullptr,
-                        st));
+                        ws, st));
 
   // ---- fof ----
   S.mark("fof");

@@ -104,7 +104,7 @@ extern "C" int cso_density_static(const int32_t* pos, int64_t n, const cso_param
   // words (the not yet written sums) into its id slot
   CellGrid g = whole_box_grid(nc, start);
   CSO_TRY(cells_bin(pos, (const uint64_t*)ssig, n, g, start, spos, sid, bad, ws, st));
-  CSO_TRY(cells_density(g, spos, (int)n, (uint32_t)p.b2, p.include_self, ssig, nullptr, st));
+  CSO_TRY(cells_density(g, spos, (int)n, (uint32_t)p.b2, p.include_self, ssig, nullptr, ws, st));
   k_unsort<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, ssig, (int)n, sigma);
   CSO_CUDA(cudaGetLastError());
   int hbad = 0;

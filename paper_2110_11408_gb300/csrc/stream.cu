@@ -413,7 +413,7 @@ int stream_step(cso_ctx* c, StreamState& S, const cso_input* in, cso_output* out
     ALLOC(uint8_t, todo, NR);
     ALLOC(long long, sig_fof, NR);
     k_window_sigma<<<G1(NR)>>>(spos, NR, g, S.rsig[k], S.rflag[k], dfresh, sig, todo);
-    CSO_TRY(cells_density(g, spos, NR, (uint32_t)p->b2, p->include_self, sig, nullptr, st, todo));
+    CSO_TRY(cells_density(g, spos, NR, (uint32_t)p->b2, p->include_self, sig, nullptr, ws, st, todo));
     k_window_after_density<<<G1(NR)>>>(spos, NR, todo, sig, S.rsig[k], S.rflag[k], sig_fof);
 
     // ---- L0 among unlabelled particles with final sums; closed groups ----
