@@ -55,6 +55,15 @@ HALO_DTYPE = np.dtype([
 ])
 
 
+RADIAL_DTYPE = np.dtype([
+    ("centre", np.int64, 3), ("d_q", np.int64, 4), ("r_q", np.float64, 4), ("vmax_n", np.int64),
+    ("vmax_d2", np.int64), ("vmax", np.float64), ("r_vmax", np.float64),
+])
+
+# fractions of the members enclosed by r_q (Table 1, r_XX_L2com)
+RADIAL_PERCENT = (25, 50, 75, 98)
+
+
 def build(force=False):
     """Compile the oracle with gcc (plain -O2, no tuning)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
@@ -95,7 +104,10 @@ def lib():
         L.orc_find_groups.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, P(OrcParams),
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int64, P(ctypes.c_int64), ctypes.c_void_p]
+        L.orc_radial.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                 ctypes.c_int64, ctypes.c_double, ctypes.c_void_p]
         assert L.orc_sizeof_halo() == ctypes.sizeof(OrcHalo) == HALO_DTYPE.itemsize
+        assert L.orc_sizeof_radial() == RADIAL_DTYPE.itemsize
         assert L.orc_sizeof_params() == ctypes.sizeof(OrcParams)
         assert L.orc_stats_count() == len(ST_NAMES)
         _lib = L
@@ -206,3 +218,16 @@ def find_groups(pos, ids, p):
         raise RuntimeError("oracle failed: %d" % rc)
     return dict(sigma=sigma, l0=l0, l1=l1, l2=l2, halos=halos[:nh.value].copy(),
                 stats=dict(zip(ST_NAMES, st.tolist())))
+
+
+def radial(pos, l1, halos, u):
+    """Radial statistics of catalogue rows (r_25/50/75/98 and V_max about the
+    L2max centre of mass), members taken from the L1 labels."""
+    pos = _pos(pos)
+    l1 = np.ascontiguousarray(l1, dtype=np.uint64)
+    halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+    out = np.zeros(max(halos.size, 1), RADIAL_DTYPE)
+    rc = lib().orc_radial(_ptr(pos), _ptr(l1), pos.shape[0], _ptr(halos), halos.size, float(u), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle radial: a row has no members")
+    return out[:halos.size].copy()

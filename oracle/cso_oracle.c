@@ -662,3 +662,107 @@ int orc_find_groups(const int32_t* pos, const uint64_t* ids, int64_t n, orc_para
 int orc_stats_count(void) { return ORC_ST_COUNT; }
 int orc_sizeof_halo(void) { return (int)sizeof(orc_halo); }
 int orc_sizeof_params(void) { return (int)sizeof(orc_params); }
+
+/* ------------------------------------------------------------------------- */
+/* radial statistics of catalogue rows (Table 1: r_XX_L2com,                  */
+/* vcirc_max_L2com, rvcirc_max_L2com; Sec. 4)                                 */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t centre[3]; /* grid point nearest the L2max com (the L1 com if no L2) */
+  int64_t d_q[4];    /* squared radius enclosing 25, 50, 75, 98 % of members  */
+  double r_q[4];     /* sqrt(d_q) / u                                         */
+  int64_t vmax_n;    /* members with d <= vmax_d2                             */
+  int64_t vmax_d2;   /* squared radius where N(<=r) / r peaks                  */
+  double vmax;       /* sqrt(vmax_n / r_vmax), units sqrt(G m_p / l_mean)      */
+  double r_vmax;     /* sqrt(vmax_d2) / u                                     */
+} orc_radial_t;
+
+static int cmp_kv_key(const void* a, const void* b) {
+  const kv_t* x = (const kv_t*)a;
+  const kv_t* y = (const kv_t*)b;
+  if (x->key != y->key) return (uint64_t)x->key < (uint64_t)y->key ? -1 : 1;
+  return x->idx < y->idx ? -1 : x->idx > y->idx;
+}
+
+/* For each catalogue row: its members are the particles whose L1 label is
+ * the row's nucleus id.  Distances are taken from the grid point nearest the
+ * centre of mass of the first L2 halo (L2max com), or of the L1 halo when it
+ * has no L2 halo, so that every distance is an exact integer.
+ *   r_XX: the k-th smallest member distance with k = ceil(XX N / 100), i.e.
+ *         the smallest member radius enclosing at least XX % of the N
+ *         members (counting members on the sphere);
+ *   V_max: the largest circular velocity v^2 = G m N(<= r) / r over member
+ *         radii r > 0, where N(<= r) counts every member at distance <= r
+ *         (the value just outside the shell at r); compared exactly as
+ *         k_a^2 d_b > k_b^2 d_a; equal values keep the smaller radius.
+ * Returns 0, or -1 if a row has no members. */
+int orc_radial(const int32_t* pos, const uint64_t* l1, int64_t n, const orc_halo* rows, int64_t nrows,
+               double u, orc_radial_t* out) {
+  static const int64_t pct[4] = {25, 50, 75, 98};
+  kv_t* byl = (kv_t*)malloc(sizeof(kv_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* d = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int rc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    byl[i].key = (int64_t)l1[i];
+    byl[i].idx = i;
+  }
+  qsort(byl, (size_t)n, sizeof(kv_t), cmp_kv_key);
+  for (int64_t r = 0; r < nrows && rc == 0; ++r) {
+    const orc_halo* h = &rows[r];
+    orc_radial_t* o = &out[r];
+    const double* com = h->n_l2 > 0 ? h->l2max_com : h->com;
+    int32_t c[3];
+    for (int k = 0; k < 3; ++k) {
+      o->centre[k] = llround(com[k]) & (ORC_BOX - 1);
+      c[k] = (int32_t)o->centre[k];
+    }
+    /* members: the run of byl with key == nucleus id (binary search) */
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) / 2;
+      if ((uint64_t)byl[mid].key < h->nucleus_id) lo = mid + 1;
+      else hi = mid;
+    }
+    int64_t m = 0;
+    for (int64_t t = lo; t < n && (uint64_t)byl[t].key == h->nucleus_id; ++t)
+      d[m++] = dist2(pos + 3 * byl[t].idx, c);
+    if (m == 0) {
+      rc = -1;
+      break;
+    }
+    qsort(d, (size_t)m, sizeof(int64_t), cmp_i64);
+    for (int q = 0; q < 4; ++q) {
+      int64_t k = (pct[q] * m + 99) / 100;
+      if (k < 1) k = 1;
+      o->d_q[q] = d[k - 1];
+      o->r_q[q] = sqrt((double)o->d_q[q]) / u;
+    }
+    int64_t bk = 0, bd = 0;
+    for (int64_t j = 0; j < m; ++j) {
+      if (d[j] == 0) continue;
+      if (j + 1 < m && d[j + 1] == d[j]) continue; /* N(<= r) counts the whole shell */
+      const int64_t k = j + 1;
+      if (bk == 0) {
+        bk = k;
+        bd = d[j];
+        continue;
+      }
+      const unsigned __int128 lhs = (unsigned __int128)(k * k) * (uint64_t)bd;
+      const unsigned __int128 rhs = (unsigned __int128)(bk * bk) * (uint64_t)d[j];
+      if (lhs > rhs) {
+        bk = k;
+        bd = d[j];
+      }
+    }
+    o->vmax_n = bk;
+    o->vmax_d2 = bd;
+    o->r_vmax = sqrt((double)bd) / u;
+    o->vmax = bk > 0 ? sqrt((double)bk / o->r_vmax) : 0.0;
+  }
+  free(byl);
+  free(d);
+  return rc;
+}
+
+int orc_sizeof_radial(void) { return (int)sizeof(orc_radial_t); }
