@@ -51,20 +51,28 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.p = None
+        self.window = None  # (t0, t1) wall-clock seconds of the timed region
 
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)  # the sampler is running before the timed region opens
         except Exception:
             self.p = None
         return self
+
+    def mark(self, which):
+        """Record the wall clock at the start (0) or end (1) of the timed region."""
+        if self.window is None:
+            self.window = [None, None]
+        self.window[which] = time.time()
 
     def __exit__(self, *a):
         self.out = ""
@@ -76,15 +84,22 @@ class ClockSampler:
                 self.p.kill()
 
     def summary(self):
+        import datetime
         rows = []
         for line in (getattr(self, "out", "") or "").strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+                ts = datetime.datetime.strptime(f[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pcap=f[8], t=ts))
             except ValueError:
                 continue
+        if self.window and None not in self.window and rows:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r["t"] <= t1]
+            # a region shorter than the sampling period keeps the sample nearest its middle
+            rows = inside or [min(rows, key=lambda r: abs(r["t"] - 0.5 * (t0 + t1)))]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         reasons = set()
@@ -224,6 +239,56 @@ def slab_stream(cso, torch, local, flags, pos, ids, meta, n_slabs=64, mean_gap_s
     return out
 
 
+def radial_stage(cso, local, flags, dpos, dids, params, steps):
+    """Radial statistics (r_25/50/75/98 and V_max about the L2max com) of every
+    L1 halo of the benchmark box: device time of the radial stage alone (an
+    optional output, outside the timed hot path), median over `steps` runs."""
+    c = cso.Context(local, flags=flags | cso.FLAG_TIMING)
+    b = cso.Buffers(dpos, dids, True, want=("l1", "radial"))
+    for _ in range(2):
+        cso.cso_find_groups(c.h, b, params)
+    ms = []
+    for _ in range(max(steps, 3)):
+        cso.cso_find_groups(c.h, b, params)
+        ms.append(cso.cso_stage_times(c.h)["radial"])
+    members = int((b.out["l1"] != -1).sum().item())
+    st = cso.cso_last_stats(c.h)
+    c.close()
+    med = statistics.median(ms)
+    return {"ms": med, "l1_haloes": st["l1_nuclei"], "catalogue_rows": int(b.cout.n_halos), "l1_members": members,
+            "members_per_s": members / (med / 1e3)}
+
+
+def _oracle_box(args):
+    side, seed = args
+    import oracle as O
+    from paper_2110_11408_gb300 import synth
+    pos, ids, meta = synth.medium_sample(side=side, seed=seed)
+    p = O.params(meta["u"])
+    t0 = time.perf_counter()
+    O.find_groups(pos, ids, p)
+    return len(pos), time.perf_counter() - t0
+
+
+def cpu_oracle_rate_all_cores(side=64, base_seed=None):
+    """The oracle as it stands, one independent box per host core in parallel
+    processes (the paper's embarrassingly parallel CPU layout): whole-job rate
+    over the wall time of the slowest process."""
+    import multiprocessing as mp
+    from paper_2110_11408_gb300 import synth
+    cores = os.cpu_count() or 1
+    seeds = [(side, (base_seed or synth.SEED0 + 40) + k) for k in range(cores)]
+    import oracle as O
+    O.build()  # compile once before the workers load it
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_box, seeds)
+    wall = time.perf_counter() - t0
+    n_tot = sum(r[0] for r in res)
+    return n_tot / wall, n_tot, wall, cores
+
+
 def cpu_oracle_rate(samples):
     """Oracle (single thread) on bounded samples of the medium recipe."""
     import oracle as O
@@ -280,6 +345,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--bins", default="", help="giant,small size bins of the batched schedule instead of autotuning")
+    ap.add_argument("--no-radial", action="store_true", help="skip timing the radial statistics stage")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -300,13 +366,17 @@ def main():
             dist.barrier()
 
     # CPU baseline first (before any device context gets forked around)
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from paper_2110_11408_gb300 import synth
         rate, n_cpu, t_cpu = cpu_oracle_rate([(64, synth.SEED0 + 21), (64, synth.SEED0 + 22)])
         cpu = {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
                "sample": "medium recipe in two seeded periodic boxes of side 64 l_mean (2 x 262,144 particles), "
                          "%.1f s of single-thread oracle time" % t_cpu}
+        rate_all, n_all, wall_all, cores = cpu_oracle_rate_all_cores()
+        cpu_all = {"value": rate_all, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                   "sample": "medium recipe, %d seeded periodic boxes of side 64 l_mean (one per core, %d particles "
+                             "in all) in parallel processes, %.1f s wall" % (cores, n_all, wall_all)}
 
     pos, ids, meta = make_workload(args.workload, rank)
     n = len(pos)
@@ -347,6 +417,8 @@ def main():
         if clk:
             clk.__enter__()
         torch.cuda.synchronize()
+        if clk:
+            clk.mark(0)
         ev0.record(stream)
         for _ in range(args.steps):
             cso.cso_find_groups(c.h, buf, params)
@@ -355,6 +427,7 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         if clk:
+            clk.mark(1)
             clk.__exit__()
         barrier()
         t = ev0.elapsed_time(ev1) / args.steps
@@ -401,6 +474,10 @@ def main():
         d2h = n * 8 * 4 + int(hb.cout.n_halos) * cso.HALO_DTYPE.itemsize
         e2e = {"value": ws * n / dt, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    radial = None
+    if not args.no_radial and ws == 1:
+        radial = radial_stage(cso, local, flags & ~cso.FLAG_TIMING, dpos, dids, params, args.steps)
+
     served = None
     if not args.no_served and ws == 1:
         served = {"boxes": served_stream(cso, torch, local, flags & ~cso.FLAG_TIMING),
@@ -434,8 +511,9 @@ def main():
         "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "n_particles": n,
                    "schedule": primary, "autotuned_bins": tuned, "l2_flush": "working set > L2 (inputs 336 MB, "
                    "cell table 1 GB)", "seed": meta["seed"]},
-        "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-        "served": served, "other_schedule": other,
+        "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all, "clocks": clocks, "served": served, "other_schedule": other,
+        "radial": radial,
         "stages_ms": stages,
         "counts": {k: stats[k] for k in ("dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows",
                                          "pairs_b", "l1_work", "l2_work", "workspace_bytes")},

@@ -119,6 +119,31 @@ typedef struct cso_input {
   uint64_t request_id;
 } cso_input;
 
+/* Radial statistics of one catalogue row (Table 1 fields r_XX_L2com,
+ * vcirc_max_L2com and rvcirc_max_L2com; Sec. 4).  Members are the particles
+ * of the L1 halo; distances are exact squared grid distances (minimum image)
+ * from `centre`, the grid point nearest the L2max centre of mass (the L1
+ * centre of mass when the halo has no L2 halo; coordinates rounded half away
+ * from zero, then wrapped into [0, 2^21)).
+ *   d_q[k]: the m-th smallest member distance, m = ceil(P_k N / 100) with
+ *           P = 25, 50, 75, 98: the smallest member radius enclosing at least
+ *           P_k % of the N members;
+ *   vmax_n, vmax_d2: the member radius r > 0 maximising v^2 = N(<= r) / r,
+ *           N(<= r) counting every member at distance <= r (decided exactly
+ *           as n_a^2 d_b > n_b^2 d_a; equal values keep the smaller radius);
+ *   r_q = sqrt(d_q) / u and r_vmax = sqrt(vmax_d2) / u in l_mean units;
+ *   vmax = sqrt(vmax_n / r_vmax) in units of sqrt(G m_particle / l_mean)
+ *           (0 when every member sits on the centre). */
+typedef struct cso_radial {
+  int64_t centre[3];
+  int64_t d_q[4];
+  double r_q[4];
+  int64_t vmax_n;
+  int64_t vmax_d2;
+  double vmax;
+  double r_vmax;
+} cso_radial;
+
 /* Outputs, caller-allocated, length n in input order (NULL = not wanted);
  * halos has room for halo_cap rows and receives the catalogue in increasing
  * nucleus id; n_halos is set to the number of rows (also on CSO_ERR_CAPACITY).
@@ -133,6 +158,9 @@ typedef struct cso_output {
   int64_t n_halos;
   int32_t on_device;
   int32_t pad_;
+  cso_radial* radial; /* halo_cap rows, row r describing halos[r]; NULL = not
+                         computed.  Whole-box requests only (CSO_ERR_ARG for a
+                         slab request). */
 } cso_output;
 
 typedef struct cso_ctx cso_ctx;
@@ -221,6 +249,12 @@ int cso_last_stats(cso_ctx* ctx, int64_t* out, int cap);
 
 /* One-line description of the last error of this thread. */
 const char* cso_last_error(void);
+
+/* Sizes in bytes of the structs above as this library was compiled:
+ * out[0..4] = sizeof cso_params, cso_halo, cso_input, cso_output, cso_radial
+ * (so that a binding can check its own layouts).  Writes min(n, 5) entries
+ * and returns 5; needs no GPU. */
+int cso_struct_sizes(int64_t* out, int n);
 
 /* --- kernel density without device allocation ---------------------------
  *

@@ -76,6 +76,14 @@ HALO_DTYPE = np.dtype([
 assert HALO_DTYPE.itemsize == ctypes.sizeof(CsoHalo)
 
 
+# one row of radial statistics (cso_radial): exact squared radii about the
+# grid point nearest the L2max com and the circular-velocity peak
+RADIAL_DTYPE = np.dtype([
+    ("centre", np.int64, 3), ("d_q", np.int64, 4), ("r_q", np.float64, 4), ("vmax_n", np.int64),
+    ("vmax_d2", np.int64), ("vmax", np.float64), ("r_vmax", np.float64),
+])
+
+
 class CsoInput(ctypes.Structure):
     _fields_ = [("pos", ctypes.c_void_p), ("ids", ctypes.c_void_p), ("n", ctypes.c_int64),
                 ("on_device", ctypes.c_int32), ("x_lo", ctypes.c_int32), ("x_hi", ctypes.c_int32),
@@ -85,7 +93,8 @@ class CsoInput(ctypes.Structure):
 class CsoOutput(ctypes.Structure):
     _fields_ = [("l0", ctypes.c_void_p), ("l1", ctypes.c_void_p), ("l2", ctypes.c_void_p),
                 ("sigma", ctypes.c_void_p), ("halos", ctypes.c_void_p), ("halo_cap", ctypes.c_int64),
-                ("n_halos", ctypes.c_int64), ("on_device", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("n_halos", ctypes.c_int64), ("on_device", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("radial", ctypes.c_void_p)]
 
 
 class CsoError(RuntimeError):
@@ -126,6 +135,7 @@ def lib(build_if_missing=True):
         L.cso_ticket_times.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double),
                                        P(ctypes.c_double)]
         L.cso_clock.restype = ctypes.c_double
+        L.cso_struct_sizes.argtypes = [P(ctypes.c_int64), ctypes.c_int]
         _lib = L
     return _lib
 
@@ -204,17 +214,20 @@ class Buffers:
             dev = pos.device if on_device else torch.device("cuda", torch.cuda.current_device())
             mk = lambda: torch.empty(n, dtype=torch.int64, device=dev)
             self.halos = torch.empty(self.halo_cap * HALO_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            self.radial = (torch.empty(self.halo_cap * RADIAL_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+                           if "radial" in want else None)
         else:
             mk = lambda: np.empty(n, np.uint64)
             self.halos = np.empty(self.halo_cap, HALO_DTYPE)
-        self.out = {k: mk() for k in want}
+            self.radial = np.empty(self.halo_cap, RADIAL_DTYPE) if "radial" in want else None
+        self.out = {k: mk() for k in want if k != "radial"}
         # x_hi > 0: the x-slab [x_lo, x_hi) of a box streamed under `request_id`
         self.cin = CsoInput(pos=_ptr(pos), ids=_ptr(ids), n=n, on_device=int(on_device), x_lo=int(x_lo),
                             x_hi=int(x_hi), request_id=int(request_id))
         self.cout = CsoOutput(l0=_ptr(self.out.get("l0")), l1=_ptr(self.out.get("l1")),
                               l2=_ptr(self.out.get("l2")), sigma=_ptr(self.out.get("sigma")),
                               halos=_ptr(self.halos), halo_cap=self.halo_cap, n_halos=0,
-                              on_device=int(self.out_device))
+                              on_device=int(self.out_device), radial=_ptr(self.radial))
 
     def result(self):
         """Outputs as numpy (copies device tensors to the host)."""
@@ -228,6 +241,12 @@ class Buffers:
             r["halos"] = raw.view(HALO_DTYPE).copy()
         else:
             r["halos"] = self.halos[: min(nh, self.halo_cap)].copy()
+        if self.radial is not None:
+            m = min(nh, self.halo_cap)
+            if self.out_device:
+                r["radial"] = self.radial[: m * RADIAL_DTYPE.itemsize].cpu().numpy().view(RADIAL_DTYPE).copy()
+            else:
+                r["radial"] = self.radial[:m].copy()
         r["n_halos"] = nh
         return r
 
@@ -321,9 +340,10 @@ class Context:
         except Exception:
             pass
 
-    def find_groups(self, pos, ids, params, on_device=None, halo_cap=None):
+    def find_groups(self, pos, ids, params, on_device=None, halo_cap=None, radial=False):
         """pos int32 [n, 3], ids uint64/int64 [n] (numpy -> host path, torch
-        CUDA -> device path).  Returns numpy outputs."""
+        CUDA -> device path).  Returns numpy outputs; radial=True adds the
+        radial statistics of every catalogue row."""
         if on_device is None:
             on_device = not isinstance(pos, np.ndarray)
         if on_device and isinstance(pos, np.ndarray):
@@ -333,7 +353,8 @@ class Context:
         if not on_device:
             pos = np.ascontiguousarray(pos, np.int32)
             ids = np.ascontiguousarray(ids).view(np.uint64)
-        b = Buffers(pos, ids, on_device, halo_cap=halo_cap)
+        want = ("l0", "l1", "l2", "sigma") + (("radial",) if radial else ())
+        b = Buffers(pos, ids, on_device, halo_cap=halo_cap, want=want)
         cso_find_groups(self.h, b, params)
         return b.result()
 

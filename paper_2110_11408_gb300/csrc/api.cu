@@ -275,6 +275,10 @@ int check_io(const cso_input* in, const cso_params* p, cso_output* out) {
     cso_set_error("halo_cap > 0 needs a halos buffer");
     return CSO_ERR_ARG;
   }
+  if (out->radial && in->x_hi > 0) {
+    cso_set_error("radial statistics are computed for whole-box requests only");
+    return CSO_ERR_ARG;
+  }
   return CSO_OK;
 }
 
@@ -286,4 +290,11 @@ extern "C" int cso_find_groups(cso_ctx* c, const cso_input* in, const cso_params
   CSO_CUDA(cudaSetDevice(c->device));
   int rc = pipeline_run(c, in, &p, out);
   return rc;
+}
+
+extern "C" int cso_struct_sizes(int64_t* out, int n) {
+  const int64_t sz[5] = {(int64_t)sizeof(cso_params), (int64_t)sizeof(cso_halo), (int64_t)sizeof(cso_input),
+                         (int64_t)sizeof(cso_output), (int64_t)sizeof(cso_radial)};
+  for (int i = 0; i < n && i < 5 && out; ++i) out[i] = sz[i];
+  return 5;
 }

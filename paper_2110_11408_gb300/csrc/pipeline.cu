@@ -14,6 +14,7 @@
 #include "cells.cuh"
 #include "compaso.cuh"
 #include "pipeline.cuh"
+#include "radial.cuh"
 
 namespace {
 
@@ -291,12 +292,14 @@ __global__ void k_catalogue_keys(const cso_halo* __restrict__ rows, const uint32
 // rows in nucleus-id order; optionally the input index of each row's nucleus
 __global__ void k_catalogue_write(const cso_halo* __restrict__ rows, const uint32_t* __restrict__ order, int m,
                                   const uint32_t* __restrict__ hnuc, const int4* __restrict__ epos,
-                                  cso_halo* __restrict__ out, uint32_t* __restrict__ out_w) {
+                                  cso_halo* __restrict__ out, uint32_t* __restrict__ out_w,
+                                  const cso_radial* __restrict__ rad, cso_radial* __restrict__ rad_out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const uint32_t h = order[i];
   out[i] = rows[h];
   if (out_w) out_w[i] = (uint32_t)epos[hnuc[h]].w;
+  if (rad_out) rad_out[i] = rad[h];
 }
 
 int readback(cso_ctx* c, const void* dev, size_t bytes) {
@@ -310,7 +313,7 @@ int readback(cso_ctx* c, const void* dev, size_t bytes) {
 }  // namespace
 
 int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, Meta* meta, uint64_t* ol1,
-               uint64_t* ol2, cso_halo** rows_out, int* nrows_out, uint32_t** rows_w_out) {
+               uint64_t* ol2, cso_halo** rows_out, int* nrows_out, uint32_t** rows_w_out, cso_radial** radial_out) {
   cudaStream_t st = c->stream;
   Workspace& ws = c->ws;
   const CellGrid& g = *gi.g;
@@ -457,12 +460,14 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   ALLOC(uint32_t, aval2, na);
   ALLOC(uint32_t, seg2, H1 + 1);
   uint32_t* ek2 = aval;
+  uint32_t* ehal2 = akey;  // L1 halo of each member element, ascending
   if (nd > 0) k_compact_assigned<<<G1(nd)>>>(ehalo, nd, aflag, gs, akey, aval, lab1);
   if (na > 0) {
     uint32_t *pk = akey, *pv = aval;
     CSO_TRY(radix_sort_32(&pk, &pv, akey2, aval2, na, bit_length_u64(H1 > 0 ? H1 - 1 : 0), ws, st));
     k_seg_bounds32<<<G1(na)>>>(pk, na, H1, seg2);
     ek2 = pv;
+    ehal2 = pk;
   }
   ALLOC(int4, epos2, na);
   ALLOC(long long, esig2, na);
@@ -533,6 +538,14 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
     k_summary<<<CL(H1), 256, 0, st>>>(seg2, epos2, ehalo2, ek2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2,
                                    h2size, 1.0 / p->l_mean_grid, p->np_min_L1, gi.x0, rows, keep);
     CSO_CUDA(cudaGetLastError());
+    cso_radial* rad = nullptr;
+    if (radial_out) {
+      S.mark("radial");
+      ALLOC(cso_radial, r1, H1);
+      rad = r1;
+      CSO_TRY(radial_run(seg2, ehal2, epos2, na, rows, H1, gi.x0, p->l_mean_grid, rad, c->pinned, ws, st));
+      S.mark("catalogue");
+    }
     ALLOC(uint32_t, kscan, H1 + 1);
     CSO_CUDA(cudaMemcpyAsync(kscan, keep, sizeof(uint32_t) * H1, cudaMemcpyDeviceToDevice, st));
     CSO_TRY(scan_u32(kscan, H1, kscan + H1, ws, st));
@@ -554,7 +567,13 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
         row_w = rw;
         *rows_w_out = rw;
       }
-      k_catalogue_write<<<G1(nrows)>>>(rows, pv, nrows, hnuc, epos, sorted_rows, row_w);
+      cso_radial* srad = nullptr;
+      if (radial_out) {
+        ALLOC(cso_radial, r2, nrows);
+        srad = r2;
+        *radial_out = r2;
+      }
+      k_catalogue_write<<<G1(nrows)>>>(rows, pv, nrows, hnuc, epos, sorted_rows, row_w, rad, srad);
       CSO_CUDA(cudaGetLastError());
     }
   }
@@ -646,7 +665,9 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   GroupsIn gin{&g, spos, sigma, sid, root, minid, nullptr, N, 0};
   int nrows = 0;
   cso_halo* sorted_rows = nullptr;
-  CSO_TRY(run_groups(c, p, gin, S, meta, ol1, ol2, &sorted_rows, &nrows, nullptr));
+  cso_radial* sorted_radial = nullptr;
+  CSO_TRY(run_groups(c, p, gin, S, meta, ol1, ol2, &sorted_rows, &nrows, nullptr,
+                     out->radial ? &sorted_radial : nullptr));
   if (count_pairs) {
     Meta hm2;
     CSO_CUDA(cudaMemcpyAsync(c->pinned, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
@@ -662,6 +683,9 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   const int ncopy = nrows <= out->halo_cap ? nrows : 0;
   if (ncopy > 0)
     CSO_CUDA(cudaMemcpyAsync(out->halos, sorted_rows, sizeof(cso_halo) * ncopy,
+                             host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  if (ncopy > 0 && out->radial)
+    CSO_CUDA(cudaMemcpyAsync(out->radial, sorted_radial, sizeof(cso_radial) * ncopy,
                              host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
 
   // ---- d2h ----

@@ -96,7 +96,8 @@ struct GroupsIn {
 // the catalogue rows (device, increasing nucleus id) of the groups taking
 // part; rows_w_out (optional) receives spos[.].w of every row's nucleus
 int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, Meta* meta, uint64_t* ol1,
-               uint64_t* ol2, cso_halo** rows_out, int* nrows_out, uint32_t** rows_w_out);
+               uint64_t* ol2, cso_halo** rows_out, int* nrows_out, uint32_t** rows_w_out,
+               cso_radial** radial_out = nullptr);
 
 size_t workspace_bytes(long long n, long long ncell, bool host_io);
 int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io);

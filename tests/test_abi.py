@@ -58,7 +58,13 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(cso.CsoParams) == 4 + 4 + 8 * 6 + 4 * 6 + 8 * 5 + 8 * 2
     assert ctypes.sizeof(cso.CsoHalo) == 8 * 19
     assert ctypes.sizeof(cso.CsoInput) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8
-    assert ctypes.sizeof(cso.CsoOutput) == 8 * 5 + 8 + 8 + 4 + 4
+    assert ctypes.sizeof(cso.CsoOutput) == 8 * 5 + 8 + 8 + 4 + 4 + 8
+    assert cso.RADIAL_DTYPE.itemsize == 8 * 15
+    # the compiled library agrees on every layout
+    sizes = (ctypes.c_int64 * 5)()
+    assert cso.lib().cso_struct_sizes(sizes, 5) == 5
+    assert list(sizes) == [ctypes.sizeof(cso.CsoParams), ctypes.sizeof(cso.CsoHalo), ctypes.sizeof(cso.CsoInput),
+                           ctypes.sizeof(cso.CsoOutput), cso.RADIAL_DTYPE.itemsize]
 
 
 def test_cosmology_scaling_matches_oracle():

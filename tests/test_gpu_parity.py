@@ -180,7 +180,7 @@ def test_medium_box_sampled_parity(ctx):
     from scipy.spatial import cKDTree
     pos, ids, meta = synth.medium()
     p, po = both_params(meta["u"], np_min_L1=1)
-    g = ctx.find_groups(pos, ids, p)
+    g = ctx.find_groups(pos, ids, p, radial=True)
     rng = np.random.default_rng(3)
     n = len(pos)
     sample = rng.choice(n, 3000, replace=False)
@@ -209,6 +209,51 @@ def test_medium_box_sampled_parity(ctx):
         for f in ("nucleus_id", "N", "R2", "l2max_id", "l2max_N", "l2_top5_N", "n_l2", "l0_id"):
             assert np.array_equal(mine[f], halos[f]), f
         np.testing.assert_allclose(mine["com"], halos["com"], rtol=1e-9, atol=1e-9 * BOX)
+        # radial statistics of the same rows, from the oracle's own labels
+        sel = np.isin(g["halos"]["nucleus_id"], halos["nucleus_id"])
+        assert_same_radial(g["radial"][sel], O.radial(pos[m], l1, halos, meta["u"]))
+
+
+def assert_same_radial(a, b):
+    assert len(a) == len(b)
+    for f in O.RADIAL_DTYPE.names:
+        if not np.array_equal(a[f], b[f]):
+            bad = np.nonzero(np.any((a[f] != b[f]).reshape(len(a), -1), axis=1))[0]
+            raise AssertionError("radial %s differs in %d of %d rows, first %s: gpu %s oracle %s"
+                                 % (f, bad.size, len(a), bad[:3], a[f][bad[:3]], b[f][bad[:3]]))
+
+
+def test_radial_statistics_tiny_box(ctx):
+    """r_25/50/75/98 and V_max of every catalogue row, bit-identical; rows
+    with and without L2 haloes (the two centre choices) both occur."""
+    pos, ids, meta = synth.tiny()
+    pg, po = both_params(U64)
+    g = ctx.find_groups(pos, ids, pg, on_device=True, radial=True)
+    o = O.find_groups(pos, ids, po)
+    assert_same(g, o)
+    assert_same_radial(g["radial"], O.radial(pos, o["l1"], o["halos"], U64))
+    assert (o["halos"]["n_l2"] == 0).any() and (o["halos"]["n_l2"] > 0).any()
+    h = ctx.find_groups(pos, ids, pg, on_device=False, radial=True)
+    assert np.array_equal(h["radial"], g["radial"])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_radial_statistics_across_periodic_corner(ctx, seed):
+    pos, ids, _ = synth.patch(extent=16.0, lo=-8.0, seed=seed)
+    pg, po = both_params(U64, np_min_L1=1)
+    g = ctx.find_groups(pos, ids, pg, radial=True)
+    o = O.find_groups(pos, ids, po)
+    assert_same(g, o)
+    assert_same_radial(g["radial"], O.radial(pos, o["l1"], o["halos"], U64))
+
+
+def test_radial_rejected_for_slab_requests(ctx):
+    pos, ids, _ = synth.patch(extent=8.0, lo=0.0, seed=1)
+    p = cso.cso_params_default(U64)
+    b = cso.Buffers(pos, ids, False, want=("l0", "radial"), x_lo=0, x_hi=1 << 16, request_id=77)
+    with pytest.raises(cso.CsoError) as e:
+        cso.cso_submit(ctx.h, b, p)
+    assert e.value.rc == cso.CSO_ERR_ARG
 
 
 # --------------------------------------------------------------------------
