@@ -299,23 +299,85 @@ __device__ __forceinline__ void uf_unite(int* parent, int a, int b) {
   }
 }
 
-// parent[s] = s for dense particles, -1 for the rest (one load answers both)
-__global__ void k_fof_init(int* __restrict__ parent, int n, const long long* __restrict__ sigma, long long T_L0) {
+// parent[s] = s for dense particles, -1 for the rest (one load answers both);
+// flag[s] = dense, scanned into the positions of the dense list
+__global__ void k_fof_init(int* __restrict__ parent, uint32_t* __restrict__ flag, int n,
+                           const long long* __restrict__ sigma, long long T_L0) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) parent[s] = sigma[s] > T_L0 ? s : -1;
+  if (s >= n) return;
+  const bool dense = sigma[s] > T_L0;
+  parent[s] = dense ? s : -1;
+  flag[s] = dense;
+}
+
+// the dense particles in cell order: FoF threads take one each, so a warp
+// holds 32 dense particles (consecutive in their cells) instead of 32 slots
+// of which only the dense ones work
+__global__ void k_dense_list(const uint32_t* __restrict__ pos_in_list, const int* __restrict__ parent, int n,
+                             int* __restrict__ didx) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n && parent[s] >= 0) didx[pos_in_list[s]] = s;
 }
 
 // First round (in the spirit of Afforest, Sutton et al. 2018): every link
 // inside a cell (each pair once).  Afterwards a cell's dense particles share
 // one tree whenever they are linked within the cell, which is the rule in
 // dense regions, so the full pass can treat such cells as units.
-__global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __restrict__ spos, int n,
+//
+// A warp whose particles share a cell streams the rest of the cell through
+// shared memory 32 particles at a time; the lane that stages a particle also
+// stages its current root (-1 if not dense), so a lane pays a forest update
+// only for a link into another tree.  A staged root that has since been
+// hooked elsewhere is still a member of its tree, so the test stays correct.
+__global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __restrict__ spos,
+                                                    const int* __restrict__ didx, const uint32_t* __restrict__ nd_ptr,
                                                     uint32_t lfof2, int* __restrict__ parent) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n || parent[s] < 0) return;
-  const int4 p = spos[s];
+  __shared__ int4 tile[8][32];
+  __shared__ int troot[8][32];
+  const int nd = (int)*nd_ptr;
+  if ((int)(blockIdx.x * blockDim.x) >= nd) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < nd;
+  const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+  if (!vmask) return;
+  const int s = valid ? didx[i] : -1;
+  const int4 p = valid ? spos[s] : make_int4(0, 0, 0, 0);
   const size_t cell = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
-  int rs = uf_root(parent, s);
+  const int src = __ffs(vmask) - 1;
+  const size_t cell0 = __shfl_sync(0xffffffffu, cell, src);
+  const bool uniform = __all_sync(0xffffffffu, !valid || cell == cell0);
+  int rs = valid ? uf_root(parent, s) : -1;
+  if (uniform) {
+    // the list is in cell order: lane src holds the warp's smallest index
+    const uint32_t lo = (uint32_t)__shfl_sync(0xffffffffu, s, src) + 1, hi = g.start[cell0 + 1];
+    for (uint32_t t0 = lo; t0 < hi; t0 += 32) {
+      const uint32_t t = t0 + lane;
+      int tr = -1;
+      if (t < hi) {
+        tile[w][lane] = spos[t];
+        if (parent[t] >= 0) tr = uf_root(parent, (int)t);
+      }
+      troot[w][lane] = tr;
+      __syncwarp();
+      const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
+      if (valid) {
+        for (int k = 0; k < m; ++k) {
+          const int rt = troot[w][k];
+          if (rt < 0 || rt == rs || (int)(t0 + k) <= s) continue;
+          const int4 q = tile[w][k];
+          const int dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+          const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+          if (d >= lfof2) continue;
+          uf_unite(parent, rs, rt);
+          rs = uf_root(parent, rs);
+        }
+      }
+      __syncwarp();
+    }
+    return;
+  }
+  if (!valid) return;
   for (uint32_t t = (uint32_t)s + 1, e = g.start[cell + 1]; t < e; ++t) {
     const int4 q = spos[t];
     const int dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
@@ -337,14 +399,16 @@ __global__ void k_fof_compress(int* __restrict__ parent, int n) {
   if (s < n && parent[s] >= 0) parent[s] = uf_root(parent, s);
 }
 
-// cell_root[c]: the common root of the dense particles of cell c, CELL_MIXED
-// if they are in several trees, CELL_EMPTY if the cell has none.  Filled
-// after compression, when parent[] holds roots.
+// The common root of the dense particles of cell c, CELL_MIXED if they are in
+// several trees, CELL_EMPTY if the cell has none, kept at slot start[c] of a
+// per-particle array (the first slot of every non-empty cell is its own), so
+// the summary costs n entries instead of one per cell of the sparse table.
+// Filled after compression, when parent[] holds roots.
 constexpr int CELL_EMPTY = -2, CELL_MIXED = -1;
 
-__global__ void k_cell_root_init(int* __restrict__ cell_root, long long ncell) {
+__global__ void k_cell_root_init(int* __restrict__ cell_root, long long n) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < ncell) cell_root[c] = CELL_EMPTY;
+  if (c < n) cell_root[c] = CELL_EMPTY;
 }
 
 __global__ void k_cell_root(const int4* __restrict__ spos, int n, CellGrid g, const int* __restrict__ parent,
@@ -355,37 +419,139 @@ __global__ void k_cell_root(const int4* __restrict__ spos, int n, CellGrid g, co
   if (r < 0) return;
   const int4 p = spos[s];
   const size_t c = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
-  int old = atomicCAS(&cell_root[c], CELL_EMPTY, r);
-  if (old != CELL_EMPTY && old != r && old != CELL_MIXED) atomicExch(&cell_root[c], CELL_MIXED);
+  int* slot = &cell_root[g.start[c]];
+  int old = atomicCAS(slot, CELL_EMPTY, r);
+  if (old != CELL_EMPTY && old != r && old != CELL_MIXED) atomicExch(slot, CELL_MIXED);
 }
 
 // Every link (d < lfof2 between dense particles) that can still join two
 // trees.  A neighbour cell whose dense particles share one tree is skipped
 // when that tree is already ours, and left after its first link otherwise
 // (the link joins the whole cell); mixed cells are walked in full, each
-// unordered pair once.
-__global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __restrict__ spos, int n,
+// unordered pair once.  Cells out of l_FoF reach of a particle (by its
+// distance to the home cell's faces) are skipped.
+//
+// A warp whose dense particles share a cell looks the 27 neighbours up once
+// (lane r holds neighbour r: run, periodic shift, tree summary), skips a
+// neighbour as soon as every lane is done with it (out of reach, or already
+// in the neighbour's tree) and otherwise streams it through shared memory
+// with the parents, each lane testing its own particle.
+__global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __restrict__ spos,
+                                                  const int* __restrict__ didx, const uint32_t* __restrict__ nd_ptr,
                                                   uint32_t lfof2, int* __restrict__ parent,
                                                   const int* __restrict__ cell_root) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n || parent[s] < 0) return;
-  const int4 p = spos[s];
+  __shared__ int4 tile[8][32];
+  __shared__ int troot[8][32];
+  const int nd = (int)*nd_ptr;
+  if ((int)(blockIdx.x * blockDim.x) >= nd) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool dense = i < nd;
+  const unsigned dmask = __ballot_sync(0xffffffffu, dense);
+  if (!dmask) return;
+  const int s = dense ? didx[i] : -1;
+  const int4 p = dense ? spos[s] : make_int4(0, 0, 0, 0);
   const int nc = g.nc;
-  const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc);
-  const XCells X = x_cells(g, grid_col(g, p.x));
-  // the x cells in order: left neighbour (or the wrapped far column), own, right
-  const int tc = grid_col(g, p.x);
-  const int xcol[3] = {X.a < tc ? X.a : X.wl, tc, X.b > tc ? X.b : X.wr};
-  const int xsh[3] = {X.a < tc ? 0 : CSO_BOX, 0, X.b > tc ? 0 : -CSO_BOX};
+  const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc), tc = grid_col(g, p.x);
+  const size_t cell = grid_cell(g, cz, cy, tc);
+  const int src = __ffs(dmask) - 1;
+  const size_t cell0 = __shfl_sync(0xffffffffu, cell, src);
+  const bool uniform = __all_sync(0xffffffffu, !dense || cell == cell0);
   // squared distance from the particle to the near faces of the neighbouring
   // cells: cells that cannot hold a particle within l_FoF are skipped
   const int gx = (p.x + g.x0) & (CSO_BOX - 1), gcx = cell_coord(gx, nc);
   const long long xl = gx - cell_lo(gcx, nc) + 1, xr = cell_lo(gcx + 1, nc) - gx;
   const long long yl = p.y - cell_lo(cy, nc) + 1, yr = cell_lo(cy + 1, nc) - p.y;
   const long long zl = p.z - cell_lo(cz, nc) + 1, zr = cell_lo(cz + 1, nc) - p.z;
-  const long long mx[3] = {xl * xl, 0, xr * xr};
   const long long R2 = lfof2;
-  int rs = uf_root(parent, s);
+  int rs = dense ? uf_root(parent, s) : -1;
+
+  if (uniform) {
+    const int ccy = __shfl_sync(0xffffffffu, cy, src), ccz = __shfl_sync(0xffffffffu, cz, src);
+    const int tc0 = __shfl_sync(0xffffffffu, tc, src);
+    const XCells X = x_cells(g, tc0);
+    // neighbours (dz, dy, dx) = (r / 9 - 1, r / 3 % 3 - 1, r % 3 - 1) within reach of this lane
+    uint32_t reach = 0;
+    if (dense) {
+      for (int r = 0; r < 27; ++r) {
+        const int dz = r / 9 - 1, dy = r / 3 % 3 - 1, dx = r % 3 - 1;
+        const long long m = (dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0)) + (dy < 0 ? yl * yl : (dy > 0 ? yr * yr : 0)) +
+                            (dx < 0 ? xl * xl : (dx > 0 ? xr * xr : 0));
+        if (m < R2) reach |= 1u << r;
+      }
+    }
+    const uint32_t need = __reduce_or_sync(0xffffffffu, reach);
+    uint32_t n_lo = 0, n_hi = 0;
+    int n_cr = CELL_EMPTY, n_sx = 0, n_sy = 0, n_sz = 0;
+    if (lane < 27 && ((need >> lane) & 1)) {
+      const int dz = lane / 9 - 1, dy = lane / 3 % 3 - 1, dx = lane % 3 - 1;
+      int sz, sy;
+      const int zz = wrap_yz(ccz + dz, nc, sz), yy = wrap_yz(ccy + dy, nc, sy);
+      const int col = dx < 0 ? (X.a < tc0 ? X.a : X.wl) : (dx > 0 ? (X.b > tc0 ? X.b : X.wr) : tc0);
+      const int sx = dx < 0 ? (X.a < tc0 ? 0 : CSO_BOX) : (dx > 0 ? (X.b > tc0 ? 0 : -CSO_BOX) : 0);
+      if (col >= 0) {
+        const size_t c = grid_cell(g, zz, yy, col);
+        n_lo = g.start[c];
+        n_hi = g.start[c + 1];
+        if (n_lo < n_hi) n_cr = cell_root[n_lo];
+        n_sx = sx;
+        n_sy = sy;
+        n_sz = sz;
+      }
+    }
+    for (uint32_t todo = __ballot_sync(0xffffffffu, n_cr != CELL_EMPTY); todo; todo &= todo - 1) {
+      const int r = __ffs(todo) - 1;
+      const uint32_t lo = __shfl_sync(0xffffffffu, n_lo, r), hi = __shfl_sync(0xffffffffu, n_hi, r);
+      const int cr = __shfl_sync(0xffffffffu, n_cr, r);
+      const int xq = p.x + __shfl_sync(0xffffffffu, n_sx, r), yq = p.y + __shfl_sync(0xffffffffu, n_sy, r),
+                zq = p.z + __shfl_sync(0xffffffffu, n_sz, r);
+      const bool unified = cr >= 0;
+      bool done = !dense || !((reach >> r) & 1);
+      if (unified && !done) done = uf_root(parent, cr) == rs;
+      if (__all_sync(0xffffffffu, done)) continue;
+      for (uint32_t t0 = lo; t0 < hi; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        int tr = -1;
+        if (t < hi) {
+          tile[w][lane] = spos[t];
+          if (parent[t] >= 0) tr = uf_root(parent, (int)t);
+        }
+        troot[w][lane] = tr;
+        __syncwarp();
+        const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
+        if (!done) {
+          for (int k = 0; k < m; ++k) {
+            const int rt = troot[w][k];
+            if (rt < 0 || (!unified && (int)(t0 + k) <= s)) continue;
+            const int4 q = tile[w][k];
+            const int ddx = xq - q.x, ddy = yq - q.y, ddz = zq - q.z;
+            const uint32_t d = (uint32_t)(ddx * ddx) + (uint32_t)(ddy * ddy) + (uint32_t)(ddz * ddz);
+            if (d >= lfof2) continue;
+            if (rt != rs) {
+              uf_unite(parent, rs, rt);
+              rs = uf_root(parent, rs);
+            }
+            if (unified) {  // one link joins the whole cell to our tree
+              done = true;
+              break;
+            }
+          }
+          // another thread may have joined the cell to our tree meanwhile
+          if (unified && !done) done = uf_root(parent, cr) == uf_root(parent, rs);
+        }
+        __syncwarp();
+        if (__all_sync(0xffffffffu, done)) break;
+      }
+    }
+    return;
+  }
+
+  if (!dense) return;
+  // the x cells in order: left neighbour (or the wrapped far column), own, right
+  const XCells X = x_cells(g, tc);
+  const int xcol[3] = {X.a < tc ? X.a : X.wl, tc, X.b > tc ? X.b : X.wr};
+  const int xsh[3] = {X.a < tc ? 0 : CSO_BOX, 0, X.b > tc ? 0 : -CSO_BOX};
+  const long long mx[3] = {xl * xl, 0, xr * xr};
   for (int dz = -1; dz <= 1; ++dz) {
     const long long mz = dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0);
     if (mz >= R2) continue;
@@ -400,12 +566,14 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
         if (xcol[k] < 0 || my + mx[k] >= R2) continue;
         const int sx = xsh[k];
         const size_t c = grid_cell(g, zz, yy, xcol[k]);
-        const int cr = cell_root[c];
+        const uint32_t c_lo = g.start[c], c_hi = g.start[c + 1];
+        if (c_lo == c_hi) continue;
+        const int cr = cell_root[c_lo];
         if (cr == CELL_EMPTY) continue;
         const bool unified = cr >= 0;
         if (unified && uf_root(parent, cr) == rs) continue;
         const int xq = p.x + sx, yq = p.y + sy, zq = p.z + sz;
-        for (uint32_t t = g.start[c], e = g.start[c + 1], it = 0; t < e; ++t, ++it) {
+        for (uint32_t t = c_lo, e = c_hi, it = 0; t < e; ++t, ++it) {
           if (!unified && (int)t <= s) continue;
           // another thread may have joined the cell to our tree meanwhile
           if (unified && (it & 15) == 15 && uf_root(parent, cr) == uf_root(parent, rs)) break;
@@ -516,17 +684,29 @@ int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int i
 
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
               const uint64_t* sid, int* parent, int* root, unsigned long long* minid, int* cell_root,
-              cudaStream_t st) {
+              Workspace& ws, cudaStream_t st) {
   if (n <= 0) return CSO_OK;
-  const long long ncell = (long long)g.ncols * g.nc * g.nc;
-  k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0);
-  k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent);
+  const size_t mark = ws.off;
+  uint32_t* flag = ws.get<uint32_t>((size_t)n + 1);
+  int* didx = ws.get<int>(n);
+  if (!flag || !didx) {
+    cso_set_error("workspace exhausted in the FoF pass");
+    return CSO_ERR_BUDGET;
+  }
+  k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, flag, n, sigma, T_L0);
+  CSO_TRY(scan_u32(flag, n, flag + n, ws, st));
+  k_dense_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(flag, parent, n, didx);
+  // the launches over the dense list are sized by n; blocks past the count
+  // (read on the device) return at once
+  const uint32_t* nd = flag + n;
+  k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, didx, nd, lfof2, parent);
   k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
-  k_cell_root_init<<<CL(cdiv(ncell, 256)), 256, 0, st>>>(cell_root, ncell);
+  k_cell_root_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(cell_root, n);
   k_cell_root<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, n, g, parent, cell_root);
-  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, lfof2, parent, cell_root);
+  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, didx, nd, lfof2, parent, cell_root);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
   CSO_CUDA(cudaGetLastError());
+  ws.off = mark;
   return CSO_OK;
 }

@@ -115,6 +115,9 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
               int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st);
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
                   unsigned long long* pairs, Workspace& ws, cudaStream_t st, const uint8_t* only = nullptr);
+// L0 friends-of-friends over the dense particles (Sigma > T_L0): root[s] (-1
+// if not dense) and minid[root] = smallest id of the group.  cell_root is
+// scratch of n ints.
 int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma, long long T_L0, uint32_t lfof2,
               const uint64_t* sid, int* parent, int* root, unsigned long long* minid, int* cell_root,
-              cudaStream_t st);
+              Workspace& ws, cudaStream_t st);

@@ -645,8 +645,8 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   ALLOC(unsigned long long, minid, n);
   {
     size_t mark = ws.off;
-    ALLOC(int, cell_root, ncell);  // per-cell tree summary, transient
-    CSO_TRY(cells_fof(g, spos, N, sigma, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, cell_root, st));
+    ALLOC(int, cell_root, n);  // per-cell tree summaries at each cell's first slot, transient
+    CSO_TRY(cells_fof(g, spos, N, sigma, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, cell_root, ws, st));
     ws.off = mark;
   }
 

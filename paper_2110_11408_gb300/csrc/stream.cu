@@ -422,8 +422,8 @@ int stream_step(cso_ctx* c, StreamState& S, const cso_input* in, cso_output* out
     ALLOC(unsigned long long, minid, NR);
     {
       size_t mark = ws.off;
-      ALLOC(int, cell_root, ncell);
-      CSO_TRY(cells_fof(g, spos, NR, sig_fof, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, cell_root, st));
+      ALLOC(int, cell_root, NR);
+      CSO_TRY(cells_fof(g, spos, NR, sig_fof, p->T_L0, (uint32_t)p->lfof2, sid, parent, root, minid, cell_root, ws, st));
       ws.off = mark;
     }
     ALLOC(int, open, NR);
