@@ -424,6 +424,131 @@ __global__ void k_cell_root(const int4* __restrict__ spos, int n, CellGrid g, co
   if (old != CELL_EMPTY && old != r && old != CELL_MIXED) atomicExch(slot, CELL_MIXED);
 }
 
+__device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __restrict__ spos, int s0,
+                                               uint32_t lfof2, int* __restrict__ parent,
+                                               const int* __restrict__ cell_root, int4* tile, int* tden, int lane) {
+  const int4 p0 = spos[s0];
+  const int nc = g.nc;
+  const int cy = cell_coord(p0.y, nc), cz = cell_coord(p0.z, nc), tc = grid_col(g, p0.x);
+  const size_t cA = grid_cell(g, cz, cy, tc);
+  const uint32_t a_lo = g.start[cA], a_hi = g.start[cA + 1];
+  const int crA = cell_root[a_lo];
+  if (crA < 0) return;  // mixed: its particles link one by one in k_fof_link
+  const XCells X = x_cells(g, tc);
+  // lane r < 13: forward neighbour 14 + r, (dz, dy, dx) = (q / 9 - 1, q / 3 % 3 - 1, q % 3 - 1)
+  uint32_t b_lo = 0, b_hi = 0;
+  int crB = CELL_EMPTY, bsx = 0, bsy = 0, bsz = 0;
+  if (lane < 13) {
+    const int q = 14 + lane;
+    const int dz = q / 9 - 1, dy = q / 3 % 3 - 1, dx = q % 3 - 1;
+    int sz, sy;
+    const int zz = wrap_yz(cz + dz, nc, sz), yy = wrap_yz(cy + dy, nc, sy);
+    const int col = dx < 0 ? (X.a < tc ? X.a : X.wl) : (dx > 0 ? (X.b > tc ? X.b : X.wr) : tc);
+    const int sx = dx < 0 ? (X.a < tc ? 0 : CSO_BOX) : (dx > 0 ? (X.b > tc ? 0 : -CSO_BOX) : 0);
+    if (col >= 0) {
+      const size_t c = grid_cell(g, zz, yy, col);
+      b_lo = g.start[c];
+      b_hi = g.start[c + 1];
+      if (b_lo < b_hi) crB = cell_root[b_lo];
+      bsx = sx;
+      bsy = sy;
+      bsz = sz;
+    }
+  }
+  for (unsigned todo = __ballot_sync(0xffffffffu, crB >= 0); todo; todo &= todo - 1) {
+    const int r = __ffs(todo) - 1;
+    const uint32_t lo = __shfl_sync(0xffffffffu, b_lo, r), hi = __shfl_sync(0xffffffffu, b_hi, r);
+    const int cb = __shfl_sync(0xffffffffu, crB, r);
+    const int sx = __shfl_sync(0xffffffffu, bsx, r), sy = __shfl_sync(0xffffffffu, bsy, r),
+              sz = __shfl_sync(0xffffffffu, bsz, r);
+    int same = 0;
+    if (lane == 0) same = uf_root(parent, crA) == uf_root(parent, cb);
+    if (__shfl_sync(0xffffffffu, same, 0)) continue;
+    bool found = false;
+    for (uint32_t a0 = a_lo; a0 < a_hi && !found; a0 += 32) {
+      const uint32_t a = a0 + lane;
+      const bool av = a < a_hi && parent[a] >= 0;
+      const int4 pa = av ? spos[a] : make_int4(0, 0, 0, 0);
+      const int xq = pa.x + sx, yq = pa.y + sy, zq = pa.z + sz;
+      if (!__any_sync(0xffffffffu, av)) continue;
+      for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
+        const uint32_t t = b0 + lane;
+        const bool tv = t < hi && parent[t] >= 0;
+        tile[lane] = tv ? spos[t] : make_int4(0, 0, 0, 0);
+        tden[lane] = tv;
+        __syncwarp();
+        const int m = hi - b0 < 32 ? (int)(hi - b0) : 32;
+        bool hit = false;
+        if (av) {
+          for (int k = 0; k < m; ++k) {
+            if (!tden[k]) continue;
+            const int4 qb = tile[k];
+            const int dx = xq - qb.x, dy = yq - qb.y, dz = zq - qb.z;
+            const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+            if (d < lfof2) {
+              hit = true;
+              break;
+            }
+          }
+        }
+        __syncwarp();
+        if (__any_sync(0xffffffffu, hit)) {
+          found = true;
+          break;
+        }
+      }
+    }
+    if (found && lane == 0) uf_unite(parent, crA, cb);
+    __syncwarp();
+  }
+}
+
+// Unified cells as units: for every cell whose dense particles share one tree
+// and each of its 13 forward neighbours (every adjacent pair of cells once)
+// that is unified too, the two trees are joined if any pair links.  A warp
+// holds the cell, 32 slots at a time, streams the neighbour through shared
+// memory, and stops at the first link.  Work per pair of dense cells is then
+// one tile in dense regions instead of a test per particle.
+__global__ void __launch_bounds__(256) k_fof_cells(CellGrid g, const int4* __restrict__ spos,
+                                                   const int* __restrict__ clist, const uint32_t* __restrict__ ncl_ptr,
+                                                   uint32_t lfof2, int* __restrict__ parent,
+                                                   const int* __restrict__ cell_root) {
+  __shared__ int4 tile[8][32];
+  __shared__ int tden[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ncl = (int)*ncl_ptr;
+  for (int wi = blockIdx.x * 8 + w; wi < ncl; wi += gridDim.x * 8) fof_cell_pairs(g, spos, clist[wi], lfof2, parent,
+                                                                                cell_root, tile[w], tden[w], lane);
+}
+
+// heads of the cells holding dense particles: position i of the dense list
+// starts a cell (the list is in cell order)
+__global__ void k_cell_heads(const int4* __restrict__ spos, CellGrid g, const int* __restrict__ didx,
+                             const uint32_t* __restrict__ nd_ptr, int n, uint32_t* __restrict__ head) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nd = (int)*nd_ptr;
+  uint32_t h = 0;
+  if (i < nd) {
+    const int4 p = spos[didx[i]];
+    const size_t c = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
+    if (i == 0) {
+      h = 1;
+    } else {
+      const int4 q = spos[didx[i - 1]];
+      h = c != grid_cell(g, cell_coord(q.z, g.nc), cell_coord(q.y, g.nc), grid_col(g, q.x));
+    }
+  }
+  head[i] = h;
+}
+
+__global__ void k_cell_list(const uint32_t* __restrict__ head_scan, const int* __restrict__ didx,
+                            const uint32_t* __restrict__ nd_ptr, int* __restrict__ clist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int)*nd_ptr) return;
+  if (head_scan[i + 1] != head_scan[i]) clist[head_scan[i]] = didx[i];
+}
+
 // Every link (d < lfof2 between dense particles) that can still join two
 // trees.  A neighbour cell whose dense particles share one tree is skipped
 // when that tree is already ours, and left after its first link otherwise
@@ -446,14 +571,18 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
   if ((int)(blockIdx.x * blockDim.x) >= nd) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool dense = i < nd;
-  const unsigned dmask = __ballot_sync(0xffffffffu, dense);
-  if (!dmask) return;
-  const int s = dense ? didx[i] : -1;
-  const int4 p = dense ? spos[s] : make_int4(0, 0, 0, 0);
+  const bool valid = i < nd;
+  if (!__any_sync(0xffffffffu, valid)) return;
+  const int s = valid ? didx[i] : -1;
+  const int4 p = valid ? spos[s] : make_int4(0, 0, 0, 0);
   const int nc = g.nc;
   const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc), tc = grid_col(g, p.x);
   const size_t cell = grid_cell(g, cz, cy, tc);
+  // particles of unified cells were linked as whole cells by k_fof_cells;
+  // here only those of mixed cells take part
+  const bool dense = valid && cell_root[g.start[cell]] == CELL_MIXED;
+  const unsigned dmask = __ballot_sync(0xffffffffu, dense);
+  if (!dmask) return;
   const int src = __ffs(dmask) - 1;
   const size_t cell0 = __shfl_sync(0xffffffffu, cell, src);
   const bool uniform = __all_sync(0xffffffffu, !dense || cell == cell0);
@@ -689,7 +818,9 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
   const size_t mark = ws.off;
   uint32_t* flag = ws.get<uint32_t>((size_t)n + 1);
   int* didx = ws.get<int>(n);
-  if (!flag || !didx) {
+  uint32_t* head = ws.get<uint32_t>((size_t)n + 1);
+  int* clist = ws.get<int>(n);
+  if (!flag || !didx || !head || !clist) {
     cso_set_error("workspace exhausted in the FoF pass");
     return CSO_ERR_BUDGET;
   }
@@ -703,6 +834,11 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
   k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
   k_cell_root_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(cell_root, n);
   k_cell_root<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, n, g, parent, cell_root);
+  // unified cells pairwise, then the particles of mixed cells
+  k_cell_heads<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, didx, nd, n, head);
+  CSO_TRY(scan_u32(head, n, head + n, ws, st));
+  k_cell_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(head, didx, nd, clist);
+  k_fof_cells<<<CL(152 * 8), 256, 0, st>>>(g, spos, clist, head + n, lfof2, parent, cell_root);
   k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, didx, nd, lfof2, parent, cell_root);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
