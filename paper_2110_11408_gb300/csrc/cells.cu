@@ -319,16 +319,19 @@ __global__ void k_dense_list(const uint32_t* __restrict__ pos_in_list, const int
   if (s < n && parent[s] >= 0) didx[pos_in_list[s]] = s;
 }
 
-// First round (in the spirit of Afforest, Sutton et al. 2018): every link
-// inside a cell (each pair once).  Afterwards a cell's dense particles share
-// one tree whenever they are linked within the cell, which is the rule in
-// dense regions, so the full pass can treat such cells as units.
+// Round one (in the spirit of Afforest, Sutton et al. 2018): each dense
+// particle tests the W = 32 slots after it in its cell, cyclically, so every
+// pair of a cell of up to 33 particles is tested and a big cell is joined by
+// a band of links around it.  The band joins almost every dense particle of
+// a big cell into one tree; the few it misses are handled one by one later.
 //
-// A warp whose particles share a cell streams the rest of the cell through
-// shared memory 32 particles at a time; the lane that stages a particle also
-// stages its current root (-1 if not dense), so a lane pays a forest update
-// only for a link into another tree.  A staged root that has since been
-// hooked elsewhere is still a member of its tree, so the test stays correct.
+// A warp whose particles share a cell streams the union of its lanes'
+// windows through shared memory; the lane that stages a particle also stages
+// its current root (-1 if not dense), so a lane pays a forest update only for
+// a link into another tree.  A staged root that has since been hooked
+// elsewhere is still a member of its tree, so the test stays correct.
+constexpr uint32_t FOF_BAND = 32;
+
 __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __restrict__ spos,
                                                     const int* __restrict__ didx, const uint32_t* __restrict__ nd_ptr,
                                                     uint32_t lfof2, int* __restrict__ parent) {
@@ -349,22 +352,30 @@ __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __re
   const bool uniform = __all_sync(0xffffffffu, !valid || cell == cell0);
   int rs = valid ? uf_root(parent, s) : -1;
   if (uniform) {
-    // the list is in cell order: lane src holds the warp's smallest index
-    const uint32_t lo = (uint32_t)__shfl_sync(0xffffffffu, s, src) + 1, hi = g.start[cell0 + 1];
-    for (uint32_t t0 = lo; t0 < hi; t0 += 32) {
-      const uint32_t t = t0 + lane;
+    // cell-relative positions: lane j tests j + 1 .. j + h (mod m)
+    const uint32_t c_lo = g.start[cell0], c_hi = g.start[cell0 + 1];
+    const uint32_t m = c_hi - c_lo;
+    const uint32_t h = m - 1 < FOF_BAND ? m - 1 : FOF_BAND;
+    const uint32_t j = valid ? (uint32_t)s - c_lo : 0;
+    const uint32_t j_first = __shfl_sync(0xffffffffu, j, src);
+    const uint32_t j_last = __shfl_sync(0xffffffffu, j, 31 - __clz(vmask));
+    const uint32_t v_end = j_last + h + 1;
+    for (uint32_t v0 = j_first + 1; v0 < v_end; v0 += 32) {
+      const uint32_t v = v0 + lane;
       int tr = -1;
-      if (t < hi) {
+      if (v < v_end) {
+        const uint32_t t = c_lo + (v < m ? v : v - m);  // v < 2m
         tile[w][lane] = spos[t];
         if (parent[t] >= 0) tr = uf_root(parent, (int)t);
       }
       troot[w][lane] = tr;
       __syncwarp();
-      const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
+      const int cnt = v_end - v0 < 32 ? (int)(v_end - v0) : 32;
       if (valid) {
-        for (int k = 0; k < m; ++k) {
+        for (int k = 0; k < cnt; ++k) {
           const int rt = troot[w][k];
-          if (rt < 0 || rt == rs || (int)(t0 + k) <= s) continue;
+          const uint32_t off = v0 + k - j;  // cyclic distance after this lane's slot
+          if (rt < 0 || rt == rs || off - 1 >= h) continue;
           const int4 q = tile[w][k];
           const int dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
           const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
@@ -378,7 +389,12 @@ __global__ void __launch_bounds__(256) k_fof_sample(CellGrid g, const int4* __re
     return;
   }
   if (!valid) return;
-  for (uint32_t t = (uint32_t)s + 1, e = g.start[cell + 1]; t < e; ++t) {
+  // lanes of several cells: each walks its own band
+  const uint32_t c_lo = g.start[cell], m = g.start[cell + 1] - c_lo;
+  const uint32_t h = m - 1 < FOF_BAND ? m - 1 : FOF_BAND;
+  for (uint32_t o = 1, j = (uint32_t)s - c_lo; o <= h; ++o) {
+    const uint32_t v = j + o;
+    const uint32_t t = c_lo + (v < m ? v : v - m);
     const int4 q = spos[t];
     const int dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
     const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
@@ -399,43 +415,118 @@ __global__ void k_fof_compress(int* __restrict__ parent, int n) {
   if (s < n && parent[s] >= 0) parent[s] = uf_root(parent, s);
 }
 
-// The common root of the dense particles of cell c, CELL_MIXED if they are in
-// several trees, CELL_EMPTY if the cell has none, kept at slot start[c] of a
-// per-particle array (the first slot of every non-empty cell is its own), so
-// the summary costs n entries instead of one per cell of the sparse table.
-// Filled after compression, when parent[] holds roots.
-constexpr int CELL_EMPTY = -2, CELL_MIXED = -1;
+// heads of the cells holding dense particles: position i of the dense list
+// starts a cell (the list is in cell order)
+__global__ void k_cell_heads(const int4* __restrict__ spos, CellGrid g, const int* __restrict__ didx,
+                             const uint32_t* __restrict__ nd_ptr, int n, uint32_t* __restrict__ head) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nd = (int)*nd_ptr;
+  uint32_t h = 0;
+  if (i < nd) {
+    const int4 p = spos[didx[i]];
+    const size_t c = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
+    if (i == 0) {
+      h = 1;
+    } else {
+      const int4 q = spos[didx[i - 1]];
+      h = c != grid_cell(g, cell_coord(q.z, g.nc), cell_coord(q.y, g.nc), grid_col(g, q.x));
+    }
+  }
+  head[i] = h;
+}
+
+__global__ void k_cell_list(const uint32_t* __restrict__ head_scan, const int* __restrict__ didx,
+                            const uint32_t* __restrict__ nd_ptr, int* __restrict__ clist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int)*nd_ptr) return;
+  if (head_scan[i + 1] != head_scan[i]) clist[head_scan[i]] = didx[i];
+}
+
+// Every cell that holds dense particles has a main tree: the tree of its
+// first dense particle after round one, kept at slot start[c] of a
+// per-particle array (the first slot of every non-empty cell is its own) so
+// the summary costs n entries instead of one per cell of the sparse table;
+// CELL_EMPTY marks cells without dense particles.  A dense particle outside
+// its cell's main tree at that point is a straggler.
+constexpr int CELL_EMPTY = -2;
 
 __global__ void k_cell_root_init(int* __restrict__ cell_root, long long n) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c < n) cell_root[c] = CELL_EMPTY;
 }
 
-__global__ void k_cell_root(const int4* __restrict__ spos, int n, CellGrid g, const int* __restrict__ parent,
-                            int* __restrict__ cell_root) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int r = parent[s];
-  if (r < 0) return;
-  const int4 p = spos[s];
+__global__ void k_cell_main(const int4* __restrict__ spos, CellGrid g, const int* __restrict__ clist,
+                            const uint32_t* __restrict__ ncl_ptr, const int* __restrict__ parent,
+                            int* __restrict__ cell_root, uint2* __restrict__ srange) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int)*ncl_ptr) return;
+  const int s0 = clist[i];
+  const int4 p = spos[s0];
   const size_t c = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
-  int* slot = &cell_root[g.start[c]];
-  int old = atomicCAS(slot, CELL_EMPTY, r);
-  if (old != CELL_EMPTY && old != r && old != CELL_MIXED) atomicExch(slot, CELL_MIXED);
+  cell_root[g.start[c]] = parent[s0];  // a root after compression
+  srange[g.start[c]] = make_uint2(0, 0);
 }
 
+// srange[start[c]] = the run of cell c in the straggler list (in cell order)
+__global__ void k_straggler_ranges(const int4* __restrict__ spos, CellGrid g, const int* __restrict__ slist,
+                                   const uint32_t* __restrict__ ns_ptr, uint2* __restrict__ srange) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ns = (int)*ns_ptr;
+  if (i >= ns) return;
+  auto cell_of = [&](int s) {
+    const int4 p = spos[s];
+    return grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
+  };
+  const size_t c = cell_of(slist[i]);
+  const uint32_t slot = g.start[c];
+  if (i == 0 || cell_of(slist[i - 1]) != c) srange[slot].x = (uint32_t)i;
+  if (i == ns - 1 || cell_of(slist[i + 1]) != c) srange[slot].y = (uint32_t)i + 1;
+}
+
+__global__ void k_stragglers(const int4* __restrict__ spos, CellGrid g, const int* __restrict__ didx,
+                             const uint32_t* __restrict__ nd_ptr, int n, const int* __restrict__ parent,
+                             const int* __restrict__ cell_root, uint8_t* __restrict__ strag,
+                             uint32_t* __restrict__ sflag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t f = 0;
+  if (i < (int)*nd_ptr) {
+    const int s = didx[i];
+    const int4 p = spos[s];
+    const size_t c = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
+    f = parent[s] != cell_root[g.start[c]];
+    strag[s] = (uint8_t)f;
+  }
+  sflag[i] = f;
+}
+
+// the stragglers in list order (flags scanned in place)
+__global__ void k_straggler_list(const uint32_t* __restrict__ sscan, const int* __restrict__ didx,
+                                 const uint32_t* __restrict__ nd_ptr, int* __restrict__ slist) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int)*nd_ptr) return;
+  if (sscan[i + 1] != sscan[i]) slist[sscan[i]] = didx[i];
+}
+
+// Round two, main trees as units: for every cell with dense particles and
+// each of its 13 forward neighbours (every adjacent pair of cells once), the
+// two main trees are joined if any pair of their members links.  A warp
+// holds the cell, 32 slots at a time, streams the neighbour through shared
+// memory and stops at the first link, so a pair of dense cells costs one
+// tile instead of a test per particle.
 __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __restrict__ spos, int s0,
                                                uint32_t lfof2, int* __restrict__ parent,
-                                               const int* __restrict__ cell_root, int4* tile, int* tden, int lane) {
+                                               const int* __restrict__ cell_root, const uint8_t* __restrict__ strag,
+                                               int4* tile, int* tmain, int lane) {
   const int4 p0 = spos[s0];
   const int nc = g.nc;
   const int cy = cell_coord(p0.y, nc), cz = cell_coord(p0.z, nc), tc = grid_col(g, p0.x);
   const size_t cA = grid_cell(g, cz, cy, tc);
   const uint32_t a_lo = g.start[cA], a_hi = g.start[cA + 1];
   const int crA = cell_root[a_lo];
-  if (crA < 0) return;  // mixed: its particles link one by one in k_fof_link
   const XCells X = x_cells(g, tc);
-  // lane r < 13: forward neighbour 14 + r, (dz, dy, dx) = (q / 9 - 1, q / 3 % 3 - 1, q % 3 - 1)
+  // lane r < 13: forward neighbour q = 14 + r, (dz, dy, dx) = (q / 9 - 1, q / 3 % 3 - 1, q % 3 - 1)
   uint32_t b_lo = 0, b_hi = 0;
   int crB = CELL_EMPTY, bsx = 0, bsy = 0, bsz = 0;
   if (lane < 13) {
@@ -467,21 +558,21 @@ __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __
     bool found = false;
     for (uint32_t a0 = a_lo; a0 < a_hi && !found; a0 += 32) {
       const uint32_t a = a0 + lane;
-      const bool av = a < a_hi && parent[a] >= 0;
+      const bool av = a < a_hi && parent[a] >= 0 && !strag[a];
       const int4 pa = av ? spos[a] : make_int4(0, 0, 0, 0);
       const int xq = pa.x + sx, yq = pa.y + sy, zq = pa.z + sz;
       if (!__any_sync(0xffffffffu, av)) continue;
       for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
         const uint32_t t = b0 + lane;
-        const bool tv = t < hi && parent[t] >= 0;
+        const bool tv = t < hi && parent[t] >= 0 && !strag[t];
         tile[lane] = tv ? spos[t] : make_int4(0, 0, 0, 0);
-        tden[lane] = tv;
+        tmain[lane] = tv;
         __syncwarp();
         const int m = hi - b0 < 32 ? (int)(hi - b0) : 32;
         bool hit = false;
         if (av) {
           for (int k = 0; k < m; ++k) {
-            if (!tden[k]) continue;
+            if (!tmain[k]) continue;
             const int4 qb = tile[k];
             const int dx = xq - qb.x, dy = yq - qb.y, dz = zq - qb.z;
             const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
@@ -503,184 +594,46 @@ __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __
   }
 }
 
-// Unified cells as units: for every cell whose dense particles share one tree
-// and each of its 13 forward neighbours (every adjacent pair of cells once)
-// that is unified too, the two trees are joined if any pair links.  A warp
-// holds the cell, 32 slots at a time, streams the neighbour through shared
-// memory, and stops at the first link.  Work per pair of dense cells is then
-// one tile in dense regions instead of a test per particle.
 __global__ void __launch_bounds__(256) k_fof_cells(CellGrid g, const int4* __restrict__ spos,
                                                    const int* __restrict__ clist, const uint32_t* __restrict__ ncl_ptr,
                                                    uint32_t lfof2, int* __restrict__ parent,
-                                                   const int* __restrict__ cell_root) {
+                                                   const int* __restrict__ cell_root,
+                                                   const uint8_t* __restrict__ strag) {
   __shared__ int4 tile[8][32];
-  __shared__ int tden[8][32];
+  __shared__ int tmain[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int ncl = (int)*ncl_ptr;
-  for (int wi = blockIdx.x * 8 + w; wi < ncl; wi += gridDim.x * 8) fof_cell_pairs(g, spos, clist[wi], lfof2, parent,
-                                                                                cell_root, tile[w], tden[w], lane);
+  for (int wi = blockIdx.x * 8 + w; wi < ncl; wi += gridDim.x * 8)
+    fof_cell_pairs(g, spos, clist[wi], lfof2, parent, cell_root, strag, tile[w], tmain[w], lane);
 }
 
-// heads of the cells holding dense particles: position i of the dense list
-// starts a cell (the list is in cell order)
-__global__ void k_cell_heads(const int4* __restrict__ spos, CellGrid g, const int* __restrict__ didx,
-                             const uint32_t* __restrict__ nd_ptr, int n, uint32_t* __restrict__ head) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int nd = (int)*nd_ptr;
-  uint32_t h = 0;
-  if (i < nd) {
-    const int4 p = spos[didx[i]];
-    const size_t c = grid_cell(g, cell_coord(p.z, g.nc), cell_coord(p.y, g.nc), grid_col(g, p.x));
-    if (i == 0) {
-      h = 1;
-    } else {
-      const int4 q = spos[didx[i - 1]];
-      h = c != grid_cell(g, cell_coord(q.z, g.nc), cell_coord(q.y, g.nc), grid_col(g, q.x));
-    }
-  }
-  head[i] = h;
-}
-
-__global__ void k_cell_list(const uint32_t* __restrict__ head_scan, const int* __restrict__ didx,
-                            const uint32_t* __restrict__ nd_ptr, int* __restrict__ clist) {
+// Round three, the stragglers one by one (a list of them): against every neighbour cell in
+// l_FoF reach (its own included), the first link into the cell's main tree
+// (skipped when that tree is already the straggler's) and every link to a
+// later straggler (each straggler pair once).  Cells out of reach of the
+// particle (by its distance to the home cell's faces) are skipped.
+__global__ void __launch_bounds__(256) k_fof_stragglers(CellGrid g, const int4* __restrict__ spos,
+                                                        const int* __restrict__ didx,
+                                                        const uint32_t* __restrict__ nd_ptr, uint32_t lfof2,
+                                                        int* __restrict__ parent, const int* __restrict__ cell_root,
+                                                        const uint8_t* __restrict__ strag,
+                                                        const uint2* __restrict__ srange) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int)*nd_ptr) return;
-  if (head_scan[i + 1] != head_scan[i]) clist[head_scan[i]] = didx[i];
-}
-
-// Every link (d < lfof2 between dense particles) that can still join two
-// trees.  A neighbour cell whose dense particles share one tree is skipped
-// when that tree is already ours, and left after its first link otherwise
-// (the link joins the whole cell); mixed cells are walked in full, each
-// unordered pair once.  Cells out of l_FoF reach of a particle (by its
-// distance to the home cell's faces) are skipped.
-//
-// A warp whose dense particles share a cell looks the 27 neighbours up once
-// (lane r holds neighbour r: run, periodic shift, tree summary), skips a
-// neighbour as soon as every lane is done with it (out of reach, or already
-// in the neighbour's tree) and otherwise streams it through shared memory
-// with the parents, each lane testing its own particle.
-__global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __restrict__ spos,
-                                                  const int* __restrict__ didx, const uint32_t* __restrict__ nd_ptr,
-                                                  uint32_t lfof2, int* __restrict__ parent,
-                                                  const int* __restrict__ cell_root) {
-  __shared__ int4 tile[8][32];
-  __shared__ int troot[8][32];
-  const int nd = (int)*nd_ptr;
-  if ((int)(blockIdx.x * blockDim.x) >= nd) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = i < nd;
-  if (!__any_sync(0xffffffffu, valid)) return;
-  const int s = valid ? didx[i] : -1;
-  const int4 p = valid ? spos[s] : make_int4(0, 0, 0, 0);
+  const int s = didx[i];
+  const int4 p = spos[s];
   const int nc = g.nc;
   const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc), tc = grid_col(g, p.x);
-  const size_t cell = grid_cell(g, cz, cy, tc);
-  // particles of unified cells were linked as whole cells by k_fof_cells;
-  // here only those of mixed cells take part
-  const bool dense = valid && cell_root[g.start[cell]] == CELL_MIXED;
-  const unsigned dmask = __ballot_sync(0xffffffffu, dense);
-  if (!dmask) return;
-  const int src = __ffs(dmask) - 1;
-  const size_t cell0 = __shfl_sync(0xffffffffu, cell, src);
-  const bool uniform = __all_sync(0xffffffffu, !dense || cell == cell0);
-  // squared distance from the particle to the near faces of the neighbouring
-  // cells: cells that cannot hold a particle within l_FoF are skipped
+  const XCells X = x_cells(g, tc);
+  const int xcol[3] = {X.a < tc ? X.a : X.wl, tc, X.b > tc ? X.b : X.wr};
+  const int xsh[3] = {X.a < tc ? 0 : CSO_BOX, 0, X.b > tc ? 0 : -CSO_BOX};
   const int gx = (p.x + g.x0) & (CSO_BOX - 1), gcx = cell_coord(gx, nc);
   const long long xl = gx - cell_lo(gcx, nc) + 1, xr = cell_lo(gcx + 1, nc) - gx;
   const long long yl = p.y - cell_lo(cy, nc) + 1, yr = cell_lo(cy + 1, nc) - p.y;
   const long long zl = p.z - cell_lo(cz, nc) + 1, zr = cell_lo(cz + 1, nc) - p.z;
-  const long long R2 = lfof2;
-  int rs = dense ? uf_root(parent, s) : -1;
-
-  if (uniform) {
-    const int ccy = __shfl_sync(0xffffffffu, cy, src), ccz = __shfl_sync(0xffffffffu, cz, src);
-    const int tc0 = __shfl_sync(0xffffffffu, tc, src);
-    const XCells X = x_cells(g, tc0);
-    // neighbours (dz, dy, dx) = (r / 9 - 1, r / 3 % 3 - 1, r % 3 - 1) within reach of this lane
-    uint32_t reach = 0;
-    if (dense) {
-      for (int r = 0; r < 27; ++r) {
-        const int dz = r / 9 - 1, dy = r / 3 % 3 - 1, dx = r % 3 - 1;
-        const long long m = (dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0)) + (dy < 0 ? yl * yl : (dy > 0 ? yr * yr : 0)) +
-                            (dx < 0 ? xl * xl : (dx > 0 ? xr * xr : 0));
-        if (m < R2) reach |= 1u << r;
-      }
-    }
-    const uint32_t need = __reduce_or_sync(0xffffffffu, reach);
-    uint32_t n_lo = 0, n_hi = 0;
-    int n_cr = CELL_EMPTY, n_sx = 0, n_sy = 0, n_sz = 0;
-    if (lane < 27 && ((need >> lane) & 1)) {
-      const int dz = lane / 9 - 1, dy = lane / 3 % 3 - 1, dx = lane % 3 - 1;
-      int sz, sy;
-      const int zz = wrap_yz(ccz + dz, nc, sz), yy = wrap_yz(ccy + dy, nc, sy);
-      const int col = dx < 0 ? (X.a < tc0 ? X.a : X.wl) : (dx > 0 ? (X.b > tc0 ? X.b : X.wr) : tc0);
-      const int sx = dx < 0 ? (X.a < tc0 ? 0 : CSO_BOX) : (dx > 0 ? (X.b > tc0 ? 0 : -CSO_BOX) : 0);
-      if (col >= 0) {
-        const size_t c = grid_cell(g, zz, yy, col);
-        n_lo = g.start[c];
-        n_hi = g.start[c + 1];
-        if (n_lo < n_hi) n_cr = cell_root[n_lo];
-        n_sx = sx;
-        n_sy = sy;
-        n_sz = sz;
-      }
-    }
-    for (uint32_t todo = __ballot_sync(0xffffffffu, n_cr != CELL_EMPTY); todo; todo &= todo - 1) {
-      const int r = __ffs(todo) - 1;
-      const uint32_t lo = __shfl_sync(0xffffffffu, n_lo, r), hi = __shfl_sync(0xffffffffu, n_hi, r);
-      const int cr = __shfl_sync(0xffffffffu, n_cr, r);
-      const int xq = p.x + __shfl_sync(0xffffffffu, n_sx, r), yq = p.y + __shfl_sync(0xffffffffu, n_sy, r),
-                zq = p.z + __shfl_sync(0xffffffffu, n_sz, r);
-      const bool unified = cr >= 0;
-      bool done = !dense || !((reach >> r) & 1);
-      if (unified && !done) done = uf_root(parent, cr) == rs;
-      if (__all_sync(0xffffffffu, done)) continue;
-      for (uint32_t t0 = lo; t0 < hi; t0 += 32) {
-        const uint32_t t = t0 + lane;
-        int tr = -1;
-        if (t < hi) {
-          tile[w][lane] = spos[t];
-          if (parent[t] >= 0) tr = uf_root(parent, (int)t);
-        }
-        troot[w][lane] = tr;
-        __syncwarp();
-        const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
-        if (!done) {
-          for (int k = 0; k < m; ++k) {
-            const int rt = troot[w][k];
-            if (rt < 0 || (!unified && (int)(t0 + k) <= s)) continue;
-            const int4 q = tile[w][k];
-            const int ddx = xq - q.x, ddy = yq - q.y, ddz = zq - q.z;
-            const uint32_t d = (uint32_t)(ddx * ddx) + (uint32_t)(ddy * ddy) + (uint32_t)(ddz * ddz);
-            if (d >= lfof2) continue;
-            if (rt != rs) {
-              uf_unite(parent, rs, rt);
-              rs = uf_root(parent, rs);
-            }
-            if (unified) {  // one link joins the whole cell to our tree
-              done = true;
-              break;
-            }
-          }
-          // another thread may have joined the cell to our tree meanwhile
-          if (unified && !done) done = uf_root(parent, cr) == uf_root(parent, rs);
-        }
-        __syncwarp();
-        if (__all_sync(0xffffffffu, done)) break;
-      }
-    }
-    return;
-  }
-
-  if (!dense) return;
-  // the x cells in order: left neighbour (or the wrapped far column), own, right
-  const XCells X = x_cells(g, tc);
-  const int xcol[3] = {X.a < tc ? X.a : X.wl, tc, X.b > tc ? X.b : X.wr};
-  const int xsh[3] = {X.a < tc ? 0 : CSO_BOX, 0, X.b > tc ? 0 : -CSO_BOX};
   const long long mx[3] = {xl * xl, 0, xr * xr};
+  const long long R2 = lfof2;
+  int rs = uf_root(parent, s);
   for (int dz = -1; dz <= 1; ++dz) {
     const long long mz = dz < 0 ? zl * zl : (dz > 0 ? zr * zr : 0);
     if (mz >= R2) continue;
@@ -693,33 +646,40 @@ __global__ void __launch_bounds__(256) k_fof_link(CellGrid g, const int4* __rest
       const int yy = wrap_yz(cy + dy, nc, sy);
       for (int k = 0; k < 3; ++k) {
         if (xcol[k] < 0 || my + mx[k] >= R2) continue;
-        const int sx = xsh[k];
         const size_t c = grid_cell(g, zz, yy, xcol[k]);
         const uint32_t c_lo = g.start[c], c_hi = g.start[c + 1];
         if (c_lo == c_hi) continue;
-        const int cr = cell_root[c_lo];
-        if (cr == CELL_EMPTY) continue;
-        const bool unified = cr >= 0;
-        if (unified && uf_root(parent, cr) == rs) continue;
-        const int xq = p.x + sx, yq = p.y + sy, zq = p.z + sz;
-        for (uint32_t t = c_lo, e = c_hi, it = 0; t < e; ++t, ++it) {
-          if (!unified && (int)t <= s) continue;
-          // another thread may have joined the cell to our tree meanwhile
-          if (unified && (it & 15) == 15 && uf_root(parent, cr) == uf_root(parent, rs)) break;
+        const int cm = cell_root[c_lo];
+        if (cm == CELL_EMPTY) continue;
+        const int xq = p.x + xsh[k], yq = p.y + sy, zq = p.z + sz;
+        // the main tree: the first link joins all of it
+        if (uf_root(parent, cm) != rs) {
+          for (uint32_t t = c_lo; t < c_hi; ++t) {
+            const int pt = parent[t];
+            if (pt < 0 || strag[t]) continue;
+            const int4 q = spos[t];
+            const int ddx = xq - q.x, ddy = yq - q.y, ddz = zq - q.z;
+            const uint32_t d = (uint32_t)(ddx * ddx) + (uint32_t)(ddy * ddy) + (uint32_t)(ddz * ddz);
+            if (d >= lfof2) continue;
+            uf_unite(parent, rs, pt);
+            rs = uf_root(parent, rs);
+            break;
+          }
+        }
+        // the cell's stragglers after this one, from its run of the list
+        const uint2 sr = srange[c_lo];
+        for (uint32_t j = sr.x; j < sr.y; ++j) {
+          const int t = didx[j];
+          if (t <= s) continue;
           const int4 q = spos[t];
           const int ddx = xq - q.x, ddy = yq - q.y, ddz = zq - q.z;
           const uint32_t d = (uint32_t)(ddx * ddx) + (uint32_t)(ddy * ddy) + (uint32_t)(ddz * ddz);
           if (d >= lfof2) continue;
-          const int pt = parent[t];
-          if (pt < 0) continue;
-          if (pt != rs) {
-            const int rt = uf_root(parent, pt);
-            if (rt != rs) {
-              uf_unite(parent, rs, rt);
-              rs = uf_root(parent, rs);
-            }
+          const int rt = uf_root(parent, t);
+          if (rt != rs) {
+            uf_unite(parent, rs, rt);
+            rs = uf_root(parent, rs);
           }
-          if (unified) break;  // one link joins the whole cell to our tree
         }
       }
     }
@@ -820,26 +780,38 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
   int* didx = ws.get<int>(n);
   uint32_t* head = ws.get<uint32_t>((size_t)n + 1);
   int* clist = ws.get<int>(n);
-  if (!flag || !didx || !head || !clist) {
+  uint8_t* strag = ws.get<uint8_t>(n);
+  uint32_t* sflag = ws.get<uint32_t>((size_t)n + 1);
+  int* slist = ws.get<int>(n);
+  uint2* srange = ws.get<uint2>(n);
+  if (!flag || !didx || !head || !clist || !strag || !sflag || !slist || !srange) {
     cso_set_error("workspace exhausted in the FoF pass");
     return CSO_ERR_BUDGET;
   }
+  // the dense list and the cells that hold dense particles; launches over
+  // them are sized by n and blocks past the counts (read on the device)
+  // return at once
   k_fof_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, flag, n, sigma, T_L0);
   CSO_TRY(scan_u32(flag, n, flag + n, ws, st));
   k_dense_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(flag, parent, n, didx);
-  // the launches over the dense list are sized by n; blocks past the count
-  // (read on the device) return at once
   const uint32_t* nd = flag + n;
-  k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, didx, nd, lfof2, parent);
-  k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
-  k_cell_root_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(cell_root, n);
-  k_cell_root<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, n, g, parent, cell_root);
-  // unified cells pairwise, then the particles of mixed cells
   k_cell_heads<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, didx, nd, n, head);
   CSO_TRY(scan_u32(head, n, head + n, ws, st));
   k_cell_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(head, didx, nd, clist);
-  k_fof_cells<<<CL(152 * 8), 256, 0, st>>>(g, spos, clist, head + n, lfof2, parent, cell_root);
-  k_fof_link<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, didx, nd, lfof2, parent, cell_root);
+  const uint32_t* ncl = head + n;
+  // round one: bands inside cells; main trees and stragglers
+  k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, didx, nd, lfof2, parent);
+  k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
+  k_cell_root_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(cell_root, n);
+  k_cell_main<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, clist, ncl, parent, cell_root, srange);
+  k_stragglers<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, didx, nd, n, parent, cell_root, strag, sflag);
+  CSO_TRY(scan_u32(sflag, n, sflag + n, ws, st));
+  k_straggler_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(sflag, didx, nd, slist);
+  k_straggler_ranges<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, slist, sflag + n, srange);
+  // round two: main trees of adjacent cells; round three: stragglers
+  k_fof_cells<<<CL(152 * 8), 256, 0, st>>>(g, spos, clist, ncl, lfof2, parent, cell_root, strag);
+  k_fof_stragglers<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, slist, sflag + n, lfof2, parent, cell_root, strag,
+                                                     srange);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);
   CSO_CUDA(cudaGetLastError());
