@@ -518,7 +518,7 @@ __global__ void k_straggler_list(const uint32_t* __restrict__ sscan, const int* 
 __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __restrict__ spos, int s0,
                                                uint32_t lfof2, int* __restrict__ parent,
                                                const int* __restrict__ cell_root, const uint8_t* __restrict__ strag,
-                                               int4* tile, int* tmain, int lane) {
+                                               int4* tile, int* tmain, int4* tileA, int* hit, int lane) {
   const int4 p0 = spos[s0];
   const int nc = g.nc;
   const int cy = cell_coord(p0.y, nc), cz = cell_coord(p0.z, nc), tc = grid_col(g, p0.x);
@@ -546,7 +546,60 @@ __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __
       bsz = sz;
     }
   }
-  for (unsigned todo = __ballot_sync(0xffffffffu, crB >= 0); todo; todo &= todo - 1) {
+  // every neighbour's tree against ours at once (a stale answer only costs a search)
+  const int rootA = uf_root(parent, crA);
+  const bool need = crB >= 0 && uf_root(parent, crB) != rootA;
+  const uint32_t mA = a_hi - a_lo, mB = b_hi - b_lo;
+  const bool small = mA <= 32 && mB <= 32;
+  if (mA <= 32 && __any_sync(0xffffffffu, need && small)) {
+    // Small pairs together: A's slots staged once, the warp's lanes take
+    // (neighbour, slot) pairs of all small neighbours in turn, and every lane
+    // tests its neighbour particle against all of A.
+    const uint32_t a = a_lo + lane;
+    const bool av = a < a_hi && parent[a] >= 0 && !strag[a];
+    tileA[lane] = av ? spos[a] : make_int4(0, 0, 0, 0);
+    if (lane < 13) hit[lane] = 0;
+    const unsigned amask = __ballot_sync(0xffffffffu, av);
+    const uint32_t cnt = (need && small) ? mB : 0;
+    uint32_t incl = cnt;
+    for (int o = 1; o < 16; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 12);
+    const uint32_t excl = incl - cnt;
+    __syncwarp();
+    for (uint32_t base = 0; base < total; base += 32) {
+      const uint32_t gi = base + lane;
+      int r = 12;
+      for (int q = 11; q >= 0; --q) {
+        const uint32_t pr = __shfl_sync(0xffffffffu, incl, q);
+        if (gi < pr) r = q;
+      }
+      const uint32_t bl = __shfl_sync(0xffffffffu, b_lo, r), ex = __shfl_sync(0xffffffffu, excl, r);
+      const int sx = __shfl_sync(0xffffffffu, bsx, r), sy = __shfl_sync(0xffffffffu, bsy, r),
+                sz = __shfl_sync(0xffffffffu, bsz, r);
+      const uint32_t t = bl + (gi - ex);
+      if (gi < total && amask && parent[t] >= 0 && !strag[t]) {
+        const int4 q = spos[t];
+        const int qx = q.x - sx, qy = q.y - sy, qz = q.z - sz;
+        for (unsigned m = amask; m; m &= m - 1) {
+          const int4 pa = tileA[__ffs(m) - 1];
+          const int dx = pa.x - qx, dy = pa.y - qy, dz = pa.z - qz;
+          const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+          if (d < lfof2) {
+            hit[r] = 1;
+            break;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < 13 && hit[lane]) uf_unite(parent, crA, crB);
+    __syncwarp();
+  }
+  // pairs with a big side: the neighbour streamed through shared memory
+  for (unsigned todo = __ballot_sync(0xffffffffu, need && !small); todo; todo &= todo - 1) {
     const int r = __ffs(todo) - 1;
     const uint32_t lo = __shfl_sync(0xffffffffu, b_lo, r), hi = __shfl_sync(0xffffffffu, b_hi, r);
     const int cb = __shfl_sync(0xffffffffu, crB, r);
@@ -569,7 +622,7 @@ __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __
         tmain[lane] = tv;
         __syncwarp();
         const int m = hi - b0 < 32 ? (int)(hi - b0) : 32;
-        bool hit = false;
+        bool found_here = false;
         if (av) {
           for (int k = 0; k < m; ++k) {
             if (!tmain[k]) continue;
@@ -577,13 +630,13 @@ __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __
             const int dx = xq - qb.x, dy = yq - qb.y, dz = zq - qb.z;
             const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
             if (d < lfof2) {
-              hit = true;
+              found_here = true;
               break;
             }
           }
         }
         __syncwarp();
-        if (__any_sync(0xffffffffu, hit)) {
+        if (__any_sync(0xffffffffu, found_here)) {
           found = true;
           break;
         }
@@ -600,11 +653,13 @@ __global__ void __launch_bounds__(256) k_fof_cells(CellGrid g, const int4* __res
                                                    const int* __restrict__ cell_root,
                                                    const uint8_t* __restrict__ strag) {
   __shared__ int4 tile[8][32];
+  __shared__ int4 tileA[8][32];
   __shared__ int tmain[8][32];
+  __shared__ int hit[8][16];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int ncl = (int)*ncl_ptr;
   for (int wi = blockIdx.x * 8 + w; wi < ncl; wi += gridDim.x * 8)
-    fof_cell_pairs(g, spos, clist[wi], lfof2, parent, cell_root, strag, tile[w], tmain[w], lane);
+    fof_cell_pairs(g, spos, clist[wi], lfof2, parent, cell_root, strag, tile[w], tmain[w], tileA[w], hit[w], lane);
 }
 
 // Round three, the stragglers one by one (a list of them): against every neighbour cell in
