@@ -599,7 +599,7 @@ struct ClusterCtl {
 struct ClusterGen {  // the leader's resumable walk over eligible candidates
   int list[CL_NT];
   int8_t peak_of[CL_NT];
-  int m, pos, peak_done, c0;
+  int m, pos, peak_done, c0, found;
 };
 
 // leader only: the next nucleus in key order (eligible and a local peak), or -1
@@ -635,13 +635,26 @@ __device__ int leader_next_nucleus(const LevelArgs& a, unsigned base, const uint
       if (tid == 0) G.peak_done = min(G.pos + CL_NT / 32, G.m);
       __syncthreads();
     }
-    const int k = G.pos;
-    const int e = G.list[k];
-    const bool take = G.peak_of[k] && !einel[e];  // eligibility may have changed since the scan
+    // The first tested candidate still eligible (a nucleus found earlier in
+    // this walk may have taken it) and a peak.  No nucleus is accepted during
+    // the walk, so one thread settles the whole tested batch.
+    if (tid == 0) {
+      int k = G.pos, found = -1;
+      for (; k < G.peak_done; ++k) {
+        const int e = G.list[k];
+        if (G.peak_of[k] && !einel[e]) {
+          found = e;
+          ++k;
+          break;
+        }
+      }
+      G.pos = k;
+      G.found = found;
+    }
     __syncthreads();
-    if (tid == 0) G.pos = k + 1;
-    __syncthreads();
-    if (take) return e;
+    const int found = G.found;
+    __syncthreads();  // every thread has read the walk state before it changes again
+    if (found >= 0) return found;
   }
 }
 
