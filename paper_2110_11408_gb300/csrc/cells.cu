@@ -42,13 +42,6 @@ __global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* 
   sid[dst] = ids[i];
 }
 
-// min(d, b2) for the squared distance d between the query and q
-__device__ __forceinline__ uint32_t dmin(int4 q, int xq, int yq, int zq, uint32_t b2) {
-  const int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
-  const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-  return d < b2 ? d : b2;
-}
-
 __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_t b2) {
   const int dx = xq - q.x, dy = yq - q.y, dz = zq - q.z;
   const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);

@@ -21,10 +21,8 @@
 
 namespace {
 
-constexpr int LV_THREADS = 256;
 constexpr int NB = 1024;      // histogram bins
 constexpr int CAP = 2048;     // largest bin resolved by an in-block sort
-constexpr int SMALL_N = 2048; // groups sorted whole
 constexpr int COUNT_N = 512;  // groups whose enclosed counts are counted directly
 
 // ---------------------------------------------------------------------------
@@ -469,7 +467,7 @@ template <int NT>
 __device__ void level_block(const LevelArgs& a, const int seg) {
   constexpr int NW = NT / 32;
   __shared__ SelShared S;
-  __shared__ int sP, sM;
+  __shared__ int sP;
   __shared__ int list[NT];
   __shared__ int peak_of[NW];
   const unsigned base = a.seg_off[seg];
