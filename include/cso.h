@@ -218,11 +218,12 @@ void cso_free(cso_ctx* ctx);
 
 /* Autotuner of the batched schedule (CSO_FLAG_BATCHED): runs the request
  * under each candidate pair of size bins -- groups above `giant` members on
- * 1024-thread blocks (4096, 16384, 65536), groups of at most `small` members
- * one per warp (32, 64) -- times the CompaSO levels, and keeps the fastest
- * pair in the context for every later call.  Outputs are written as by
- * cso_find_groups (identical for every pair).  giant/small (may be NULL)
- * receive the choice. */
+ * 8-CTA thread-block clusters (16384, 65536, 262144), groups of at most
+ * `small` members one per warp (32, 64); groups above max(giant / 16, 512)
+ * run on 1024-thread blocks and the rest on 256-thread blocks -- times the
+ * CompaSO levels, and keeps the fastest pair in the context for every later
+ * call.  Outputs are written as by cso_find_groups (identical for every
+ * pair).  giant/small (may be NULL) receive the choice. */
 int cso_autotune(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out, int32_t* giant,
                  int32_t* small);
 

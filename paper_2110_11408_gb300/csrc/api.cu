@@ -132,6 +132,8 @@ extern "C" int cso_init(cso_ctx** out, int device, size_t budget, uint32_t flags
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, sizeof(long long) * 64);
   for (int i = 0; e == cudaSuccess && i <= CSO_MAX_STAGES; ++i) e = cudaEventCreate(&c->ev[i]);
   if (e != cudaSuccess) {
@@ -153,6 +155,9 @@ extern "C" void cso_free(cso_ctx* c) {
   for (int i = 0; i <= CSO_MAX_STAGES; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->side) cudaStreamSynchronize(c->side);
+  if (c->side2) cudaStreamSynchronize(c->side2);
+  if (c->join2) cudaEventDestroy(c->join2);
+  if (c->side2) cudaStreamDestroy(c->side2);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);
@@ -230,7 +235,7 @@ extern "C" int cso_set_schedule(cso_ctx* c, int32_t giant, int32_t small) {
 extern "C" int cso_autotune(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out,
                             int32_t* giant, int32_t* small) {
   if (!c) return CSO_ERR_ARG;
-  static const int giants[] = {4096, 16384, 65536};
+  static const int giants[] = {16384, 65536, 262144};
   static const int smalls[] = {32, 64};
   const uint32_t saved = c->flags;
   c->flags |= CSO_FLAG_TIMING | CSO_FLAG_BATCHED;

@@ -1059,7 +1059,7 @@ __global__ void __launch_bounds__(256) k_level_warp(LevelArgs a, const uint32_t*
 }
 
 // segment sizes as descending sort keys, and the size-bin counts
-__global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int giant, int small,
+__global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int giant, int large, int small,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ val, unsigned* __restrict__ counts) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= nseg) return;
@@ -1067,6 +1067,7 @@ __global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int 
   key[g] = 0xffffffffu - sz;
   val[g] = (uint32_t)g;
   if (sz > (uint32_t)giant) atomicAdd(&counts[0], 1u);
+  else if (sz > (uint32_t)large) atomicAdd(&counts[1], 1u);
   else if (sz <= (uint32_t)small) atomicAdd(&counts[2], 1u);
 }
 
@@ -1101,7 +1102,8 @@ int level_run(const LevelArgs& a, cudaStream_t st) {
 }
 
 int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws, cudaStream_t st,
-                      cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, unsigned* host_counts) {
+                      cudaStream_t side, cudaStream_t side2, cudaEvent_t fork, cudaEvent_t join,
+                      cudaEvent_t join2, unsigned* host_counts) {
   if (a.nseg <= 0) return CSO_OK;
   size_t mark = ws.off;
   uint32_t* key = ws.get<uint32_t>(a.nseg);
@@ -1114,25 +1116,37 @@ int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws
     return CSO_ERR_BUDGET;
   }
   CSO_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned), st));
-  k_seg_sizes<<<CL(cdiv(a.nseg, 256)), 256, 0, st>>>(a.seg_off, a.nseg, sc.giant, sc.small, key, val, counts);
+  k_seg_sizes<<<CL(cdiv(a.nseg, 256)), 256, 0, st>>>(a.seg_off, a.nseg, sc.giant, sc.large(), sc.small, key, val,
+                                                     counts);
   // largest groups first: giants start at once, the rest fill in behind them
   uint32_t *pk = key, *pv = val;
   CSO_TRY(radix_sort_32(&pk, &pv, key2, val2, a.nseg, 32, ws, st));
   CSO_CUDA(cudaMemcpyAsync(host_counts, counts, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   CSO_CUDA(cudaStreamSynchronize(st));
-  const int ng = (int)host_counts[0], ns = (int)host_counts[2], nm = a.nseg - ng - ns;
+  const int ng = (int)host_counts[0], nl = (int)host_counts[1], ns = (int)host_counts[2];
+  const int nm = a.nseg - ng - nl - ns;
+  // giants and large groups on their own streams, concurrent with the rest
+  if (ng > 0 || nl > 0) CSO_CUDA(cudaEventRecord(fork, st));
   if (ng > 0) {
-    CSO_CUDA(cudaEventRecord(fork, st));
     CSO_CUDA(cudaStreamWaitEvent(side, fork, 0));
     k_level_cluster<<<CL(ng * CL_CS), CL_NT, 0, side>>>(a, pv);
     CSO_CUDA(cudaGetLastError());
   }
-  if (nm > 0) k_level<256><<<CL(nm), 256, 0, st>>>(a, pv + ng);
-  if (ns > 0) k_level_warp<<<CL(cdiv(ns, 8)), 256, 0, st>>>(a, pv + ng + nm, ns);
+  if (nl > 0) {
+    CSO_CUDA(cudaStreamWaitEvent(side2, fork, 0));
+    k_level<1024><<<CL(nl), 1024, 0, side2>>>(a, pv + ng);
+    CSO_CUDA(cudaGetLastError());
+  }
+  if (nm > 0) k_level<256><<<CL(nm), 256, 0, st>>>(a, pv + ng + nl);
+  if (ns > 0) k_level_warp<<<CL(cdiv(ns, 8)), 256, 0, st>>>(a, pv + ng + nl + nm, ns);
   CSO_CUDA(cudaGetLastError());
   if (ng > 0) {
     CSO_CUDA(cudaEventRecord(join, side));
     CSO_CUDA(cudaStreamWaitEvent(st, join, 0));
+  }
+  if (nl > 0) {
+    CSO_CUDA(cudaEventRecord(join2, side2));
+    CSO_CUDA(cudaStreamWaitEvent(st, join2, 0));
   }
   ws.off = mark;
   return CSO_OK;

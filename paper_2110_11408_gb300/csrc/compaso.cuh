@@ -42,17 +42,20 @@ struct LevelArgs {
   int nb;                   // histogram bins (<= 1024)
 };
 
-// size bins of the batched schedule: groups above `giant` members run on a
-// 1024-thread block, groups up to `small` members on one warp, the rest on a
-// 256-thread block; largest first
+// size bins of the batched schedule: groups above `giant` members run on an
+// 8-CTA thread-block cluster, groups above large() on a 1024-thread block,
+// groups up to `small` members on one warp, the rest on a 256-thread block;
+// largest first within each bin
 struct LevelSchedule {
   int giant = 16384;
   int small = 64;
+  int large() const { return giant / 16 > 512 ? giant / 16 : 512; }
 };
 
 int level_run(const LevelArgs& a, cudaStream_t st);
 int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws, cudaStream_t st,
-                      cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, unsigned* host_counts);
+                      cudaStream_t side, cudaStream_t side2, cudaEvent_t fork, cudaEvent_t join,
+                      cudaEvent_t join2, unsigned* host_counts);
 int level_halo(int nseg, const uint32_t* seg_off, const uint32_t* nnuc, const uint32_t* hbase, const int* eslot,
                const uint32_t* nuc_member, const long long* nuc_R2, int* ehalo, uint32_t* hnuc, long long* hR2,
                uint32_t* hseg, cudaStream_t st);

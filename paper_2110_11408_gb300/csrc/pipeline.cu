@@ -82,6 +82,47 @@ __global__ void k_make_keys(const uint32_t* __restrict__ dl, int nd, const int* 
   val[k] = s;
 }
 
+// (group, Sigma desc) in one 64-bit key; the id tie-break is settled after
+// the sort by k_tie_fix
+__global__ void k_make_keys64(const uint32_t* __restrict__ dl, int nd, const int* __restrict__ root,
+                              const uint32_t* __restrict__ rscan, const long long* __restrict__ sigma,
+                              unsigned long long sigma_max, int bits_sig, uint64_t* __restrict__ key,
+                              uint32_t* __restrict__ val) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nd) return;
+  uint32_t s = dl[k];
+  key[k] = ((uint64_t)rscan[root[s]] << bits_sig) | (sigma_max - (unsigned long long)sigma[s]);
+  val[k] = s;
+}
+
+// Runs of equal (group, Sigma) keys, ordered by id: the first thread of a run
+// sorts it by insertion (runs are almost always single elements).  A run
+// longer than TIE_RUN_MAX is left alone and raises *overflow, and the caller
+// sorts again with the id inside the key.
+constexpr int TIE_RUN_MAX = 64;
+
+__global__ void k_tie_fix(const uint64_t* __restrict__ key, uint32_t* __restrict__ val, int nd,
+                          const uint64_t* __restrict__ sid, int* __restrict__ overflow) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k + 1 >= nd || key[k + 1] != key[k] || (k > 0 && key[k - 1] == key[k])) return;
+  int e = k + 1;
+  while (e < nd && key[e] == key[k] && e - k <= TIE_RUN_MAX) ++e;
+  if (e - k > TIE_RUN_MAX) {
+    atomicExch(overflow, 1);
+    return;
+  }
+  for (int i = k + 1; i < e; ++i) {
+    const uint32_t v = val[i];
+    const uint64_t id = sid[v];
+    int j = i - 1;
+    while (j >= k && sid[val[j]] > id) {
+      val[j + 1] = val[j];
+      --j;
+    }
+    val[j + 1] = v;
+  }
+}
+
 __global__ void k_seg_bounds128(const uint64_t* __restrict__ khi, const uint64_t* __restrict__ klo, int nd,
                                 int gshift, int nseg, uint32_t* __restrict__ seg_off) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -377,12 +418,31 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   ALLOC(uint64_t, eid, nd);
   uint32_t* gs = kval;
   if (nd > 0) {
-    k_make_keys<<<G1(nd)>>>(dl, nd, root, rscan, sigma, sid, hm.sigma_max, bits_id, bits_sig, khi, klo, kval);
-    uint64_t *ph = khi, *pl = klo;
+    // (group, Sigma desc) fits one 64-bit key in every box the cell table
+    // admits: sort by it, then order the rare runs of equal sums by id
+    bool full = bits_sig + bits_g > 64;
+    uint64_t *ph = nullptr, *pl = klo;
     uint32_t* pv = kval;
-    int bits = bits_id + bits_sig + bits_g;
-    CSO_TRY(radix_sort_128(&ph, &pl, &pv, khi2, klo2, kval2, nd, bits, ws, st));
-    k_seg_bounds128<<<G1(nd)>>>(bits > 64 ? ph : nullptr, pl, nd, bits_sig + bits_id, G, seg1);
+    if (!full) {
+      k_make_keys64<<<G1(nd)>>>(dl, nd, root, rscan, sigma, hm.sigma_max, bits_sig, klo, kval);
+      CSO_TRY(radix_sort_128(&ph, &pl, &pv, nullptr, klo2, kval2, nd, bits_sig + bits_g, ws, st));
+      int* overflow = &meta->tie_overflow;
+      k_tie_fix<<<G1(nd)>>>(pl, pv, nd, sid, overflow);
+      CSO_CUDA(cudaMemcpyAsync(c->pinned, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CSO_CUDA(cudaStreamSynchronize(st));
+      full = *(int*)c->pinned != 0;
+      if (full) CSO_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int), st));
+      else k_seg_bounds128<<<G1(nd)>>>(nullptr, pl, nd, bits_sig, G, seg1);
+    }
+    if (full) {
+      k_make_keys<<<G1(nd)>>>(dl, nd, root, rscan, sigma, sid, hm.sigma_max, bits_id, bits_sig, khi, klo, kval);
+      ph = khi;
+      pl = klo;
+      pv = kval;
+      int bits = bits_id + bits_sig + bits_g;
+      CSO_TRY(radix_sort_128(&ph, &pl, &pv, khi2, klo2, kval2, nd, bits, ws, st));
+      k_seg_bounds128<<<G1(nd)>>>(bits > 64 ? ph : nullptr, pl, nd, bits_sig + bits_id, G, seg1);
+    }
     gs = pv;
     k_gather1<<<G1(nd)>>>(gs, nd, spos, sigma, sid, epos, esig, eid);
     CSO_CUDA(cudaGetLastError());
@@ -430,7 +490,8 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   const bool batched = (c->flags & CSO_FLAG_BATCHED) != 0;
   const LevelSchedule sched = c->sched;
   unsigned* hcounts = (unsigned*)(c->pinned + 32);
-  if (batched) CSO_TRY(level_run_batched(L1, sched, ws, st, c->side, c->fork, c->join, hcounts));
+  if (batched)
+    CSO_TRY(level_run_batched(L1, sched, ws, st, c->side, c->side2, c->fork, c->join, c->join2, hcounts));
   else CSO_TRY(level_run(L1, st));
 
   // ---- prep2: L1 haloes, their members in key order, peaks within L1 ----
@@ -496,7 +557,8 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   L2.nnuc = nnuc2;
   L2.work = &meta->work2;
   // edold / einel / ed are reused (na <= nd)
-  if (batched) CSO_TRY(level_run_batched(L2, sched, ws, st, c->side, c->fork, c->join, hcounts));
+  if (batched)
+    CSO_TRY(level_run_batched(L2, sched, ws, st, c->side, c->side2, c->fork, c->join, c->join2, hcounts));
   else CSO_TRY(level_run(L2, st));
 
   // ---- output ----

@@ -26,8 +26,9 @@ struct ServedState;
 struct cso_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
-  cudaStream_t side = nullptr;  // second stream of the batched schedule (giant groups)
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side = nullptr;   // second stream of the batched schedule (giant groups)
+  cudaStream_t side2 = nullptr;  // third stream (large groups)
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
   size_t budget = 0;
   uint32_t flags = 0;
   Workspace ws;
@@ -50,7 +51,7 @@ struct Meta {  // device counters read back by the host
   unsigned long long sigma_max, id_max;
   unsigned long long pairs, work1, work2;
   int bad;
-  unsigned pad;
+  int tie_overflow;  // a run of equal (group, Sigma) keys too long for k_tie_fix
 };
 
 // dense particles taking part (all, or those of selected groups) and group roots
