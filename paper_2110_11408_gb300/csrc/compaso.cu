@@ -592,67 +592,40 @@ struct ClusterCtl {
   int from;                 // next bin to examine after a gather
   int bin;                  // bin being gathered
   unsigned in_window;
+  int blo, bn, bend;        // candidate batch of the nucleus walk
 };
 
 struct ClusterGen {  // the leader's resumable walk over eligible candidates
   int list[CL_NT];
   int8_t peak_of[CL_NT];
-  int m, pos, peak_done, c0, found;
+  int m, pos, c0;
 };
 
-// leader only: the next nucleus in key order (eligible and a local peak), or -1
-__device__ int leader_next_nucleus(const LevelArgs& a, unsigned base, const uint8_t* einel, const uint32_t* egs,
-                                   int P, int glabel, ClusterGen& G, SelShared& S) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  while (true) {
-    if (G.pos >= G.m) {
-      if (G.c0 >= P) return -1;
-      const int j = G.c0 + tid;
-      const unsigned f = (j < P && !einel[j]) ? 1u : 0u;
-      unsigned excl;
-      const unsigned m = block_scan<CL_NT>(f, excl, S.sw);
-      if (f) G.list[excl] = j;
-      __syncthreads();
-      if (tid == 0) {
-        G.m = (int)m;
-        G.pos = 0;
-        G.peak_done = 0;
-        G.c0 += CL_NT;
-      }
-      __syncthreads();
-      continue;
-    }
-    if (G.pos >= G.peak_done) {  // peak flags for the next 32 candidates, a warp each
-      const int k = G.pos + warp;
-      if (k < G.m) {
-        const int e = G.list[k];
-        const bool ok = !einel[e] && warp_is_peak(a, egs[e], glabel);
-        if (lane == 0) G.peak_of[k] = ok;
-      }
-      __syncthreads();
-      if (tid == 0) G.peak_done = min(G.pos + CL_NT / 32, G.m);
-      __syncthreads();
-    }
-    // The first tested candidate still eligible (a nucleus found earlier in
-    // this walk may have taken it) and a peak.  No nucleus is accepted during
-    // the walk, so one thread settles the whole tested batch.
+// Leader only: refill the candidate list when it is used up (the eligible
+// members among the next CL_NT above the stop level, in key order) and
+// publish the next batch of up to CL_CS * 32 untested candidates in C.blo /
+// C.bn, or C.bend = 1 when none remain.  Every CTA of the cluster then tests
+// one candidate of the batch per warp.
+__device__ void leader_next_batch(const uint8_t* einel, int P, ClusterGen& G, ClusterCtl& C, SelShared& S) {
+  const int tid = threadIdx.x;
+  while (G.pos >= G.m && G.c0 < P) {
+    const int j = G.c0 + tid;
+    const unsigned f = (j < P && !einel[j]) ? 1u : 0u;
+    unsigned excl;
+    const unsigned m = block_scan<CL_NT>(f, excl, S.sw);
+    if (f) G.list[excl] = j;
+    __syncthreads();
     if (tid == 0) {
-      int k = G.pos, found = -1;
-      for (; k < G.peak_done; ++k) {
-        const int e = G.list[k];
-        if (G.peak_of[k] && !einel[e]) {
-          found = e;
-          ++k;
-          break;
-        }
-      }
-      G.pos = k;
-      G.found = found;
+      G.m = (int)m;
+      G.pos = 0;
+      G.c0 += CL_NT;
     }
     __syncthreads();
-    const int found = G.found;
-    __syncthreads();  // every thread has read the walk state before it changes again
-    if (found >= 0) return found;
+  }
+  if (tid == 0) {
+    C.bend = G.pos >= G.m;
+    C.blo = G.pos;
+    C.bn = min(G.m - G.pos, CL_CS * 32);
   }
 }
 
@@ -888,21 +861,52 @@ __global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
     C.P = lo;
     G.m = 0;
     G.pos = 0;
-    G.peak_done = 0;
     G.c0 = 0;
   }
+  ClusterGen* LG = cluster.map_shared_rank(&G, 0);
+  const int warp = tid >> 5, lane = tid & 31;
   const int glabel = a.slab[egs[0]];
   const long long anum2 = (long long)a.alpha_num * a.alpha_num, aden2 = (long long)a.alpha_den * a.alpha_den;
   cluster.sync();  // slots and flags initialised everywhere
   int nn = 0;
   while (true) {
-    if (leader) {
-      __syncthreads();
-      const int e = leader_next_nucleus(a, base, einel, egs, C.P, glabel, G, S);
-      if (tid == 0) C.e = e;
+    // Step 2 walk: the next candidate in key order that is eligible and a
+    // local peak.  The leader hands out batches; every warp of every CTA
+    // peak-tests one candidate and stores the flag in the leader's shared
+    // memory; the leader's thread 0 takes the first candidate of the batch
+    // that passes (no nucleus is accepted during the walk, so the batch is
+    // settled at once).  Every CTA passes the same barriers: the exits are
+    // read from the leader after a barrier.
+    int e = -1;
+    while (true) {
+      if (leader) leader_next_batch(einel, C.P, G, C, S);
+      cluster.sync();  // batch published
+      if (LC->bend) break;
+      const int blo = LC->blo, bn = LC->bn;
+      const int k = blo + rank * 32 + warp;
+      if (k < blo + bn) {
+        const int ek = LG->list[k];
+        const bool ok = !einel[ek] && warp_is_peak(a, egs[ek], glabel);
+        if (lane == 0) LG->peak_of[k] = (int8_t)ok;
+      }
+      cluster.sync();  // peak flags in the leader's shared memory
+      if (leader && tid == 0) {
+        int kk = C.blo, found = -1;
+        for (const int kend = C.blo + C.bn; kk < kend; ++kk) {
+          const int ec = G.list[kk];
+          if (G.peak_of[kk] && !einel[ec]) {
+            found = ec;
+            ++kk;
+            break;
+          }
+        }
+        G.pos = kk;
+        C.e = found;
+      }
+      cluster.sync();  // walk decision published
+      e = LC->e;
+      if (e >= 0) break;
     }
-    cluster.sync();
-    const int e = LC->e;
     if (e < 0) break;
     const int4 pc = epos[e];
     const long long R2 = cluster_r_search(cluster, epos, ed, n, lo_r, hi_r, pc, a.pc, S, C, a.cap, a.nb);
