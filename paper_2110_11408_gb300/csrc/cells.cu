@@ -34,12 +34,13 @@ __global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, CellG
 __global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n,
                                int x0, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
                                const uint32_t* __restrict__ start, int4* __restrict__ spos,
-                               uint64_t* __restrict__ sid) {
+                               uint64_t* __restrict__ sid, uint32_t* __restrict__ inv) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t dst = start[key[i]] + rank[i];
   spos[dst] = make_int4((pos[3 * i] - x0) & (CSO_BOX - 1), pos[3 * i + 1], pos[3 * i + 2], (int)i);
   sid[dst] = ids[i];
+  if (inv) inv[i] = dst;
 }
 
 __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_t b2) {
@@ -773,7 +774,7 @@ int cells_choose(long long b2, int* nc_out) {
 }
 
 int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGrid& g, uint32_t* start,
-              int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st) {
+              int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st, uint32_t* inv) {
   long long ncell = (long long)g.ncols * g.nc * g.nc;
   size_t mark = ws.off;
   uint32_t* key = ws.get<uint32_t>(n);
@@ -789,7 +790,7 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
   }
   CSO_TRY(scan_u32(start, ncell + 1, nullptr, ws, st));
   if (n > 0) {
-    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g.x0, key, rank, start, spos, sid);
+    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g.x0, key, rank, start, spos, sid, inv);
     CSO_CUDA(cudaGetLastError());
   }
   ws.off = mark;

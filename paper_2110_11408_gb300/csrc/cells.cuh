@@ -111,8 +111,10 @@ __device__ __forceinline__ void for_stencil(const CellGrid& g, int x, int y, int
 }
 
 int cells_choose(long long b2, int* nc_out);
+// Counting sort of the particles into the cell table; inv (optional, n
+// entries) receives the sorted slot of every input particle.
 int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGrid& g, uint32_t* start,
-              int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st);
+              int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st, uint32_t* inv = nullptr);
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
                   unsigned long long* pairs, Workspace& ws, cudaStream_t st, const uint8_t* only = nullptr);
 // L0 friends-of-friends over the dense particles (Sigma > T_L0): root[s] (-1

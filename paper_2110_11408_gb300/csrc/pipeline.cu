@@ -188,16 +188,18 @@ __global__ void k_fill_u64(uint64_t* p, long long n, uint64_t v) {
   if (i < n) p[i] = v;
 }
 
-__global__ void k_out_cells(const int4* __restrict__ spos, int n, const long long* __restrict__ sigma,
+// kernel sums and L0 labels in input order: thread i reads its particle's
+// sorted slot (scattered reads, coalesced writes)
+__global__ void k_out_cells(const uint32_t* __restrict__ inv, int n, const long long* __restrict__ sigma,
                             const int* __restrict__ root, const unsigned long long* __restrict__ minid,
                             int64_t* __restrict__ osig, uint64_t* __restrict__ ol0) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  int orig = spos[s].w;
-  if (osig) osig[orig] = sigma[s];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t s = inv[i];
+  if (osig) osig[i] = sigma[s];
   if (ol0) {
     int r = root[s];
-    ol0[orig] = r >= 0 ? minid[r] : NONE;
+    ol0[i] = r >= 0 ? minid[r] : NONE;
   }
 }
 
@@ -691,7 +693,8 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   ALLOC(int4, spos, n);
   ALLOC(uint64_t, sid, n);
   CellGrid g = whole_box_grid(nc, start);
-  CSO_TRY(cells_bin(pos, ids, n, g, start, spos, sid, &meta->bad, ws, st));
+  ALLOC(uint32_t, inv, n);
+  CSO_TRY(cells_bin(pos, ids, n, g, start, spos, sid, &meta->bad, ws, st, inv));
 
   // ---- density ----
   S.mark("density");
@@ -738,7 +741,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
     c->stats[6] = (int64_t)hm2.pairs;
   }
   S.mark("output");
-  k_out_cells<<<G1(n)>>>(spos, N, sigma, root, minid, osig, ol0);
+  k_out_cells<<<G1(n)>>>(inv, N, sigma, root, minid, osig, ol0);
   CSO_CUDA(cudaGetLastError());
   out->n_halos = nrows;
   c->stats[5] = nrows;
