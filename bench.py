@@ -36,6 +36,10 @@ WORKLOADS = {
                       "[20, 2e4]"),
 }
 OPS_PER_PAIR = 11  # 3 sub, 3 mul, 2 add for d; compare; b2 - d; accumulate
+# DRAM bytes (read + write) of one k_density launch on the medium box, from
+# the single-pass ncu capture summarised in profiles/density_medium_dram.md;
+# valid for that kernel as it stands, and only for the medium workload
+DENSITY_DRAM_BYTES = {"medium": 3.25e9 + 135.21e6}
 
 
 def load_peaks():
@@ -499,7 +503,8 @@ def main():
     if dens_ms:
         achieved = stats["pairs_b"] * OPS_PER_PAIR / (dens_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "k_density", "achieved": achieved, "peak": alu_peak,
-                "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+                "unit": "Tops/s", "frac": achieved / alu_peak,
+                "traffic": DENSITY_DRAM_BYTES.get(args.workload),
                 "peak_source": "derived: 152 SMs x 128 int32 lanes x %.0f MHz (max SM clock, %s peaks file)"
                                % (sm_mhz, peak_src),
                 "algorithmic": "%d pairs within b x %d int ops" % (stats["pairs_b"], OPS_PER_PAIR)}
