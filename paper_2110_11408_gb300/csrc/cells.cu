@@ -31,16 +31,29 @@ __global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, CellG
   rank[i] = atomicAdd(&count[k], 1u);
 }
 
-__global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n,
-                               int x0, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
-                               const uint32_t* __restrict__ start, int4* __restrict__ spos,
-                               uint64_t* __restrict__ sid, uint32_t* __restrict__ inv) {
+// Slot of every particle: only the 4-byte input index is scattered (perm);
+// the positions and ids follow by a gather in slot order, so the 24 bytes a
+// particle carries are read from scattered places and written in sequence
+// (scattered writes of partial sectors cost a sector read each).
+__global__ void k_cell_scatter(long long n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+                               const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
+                               uint32_t* __restrict__ inv) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t dst = start[key[i]] + rank[i];
-  spos[dst] = make_int4((pos[3 * i] - x0) & (CSO_BOX - 1), pos[3 * i + 1], pos[3 * i + 2], (int)i);
-  sid[dst] = ids[i];
+  perm[dst] = (uint32_t)i;
   if (inv) inv[i] = dst;
+}
+
+__global__ void k_cell_gather(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n, int x0,
+                              const uint32_t* __restrict__ perm, int4* __restrict__ spos,
+                              uint64_t* __restrict__ sid) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint32_t i = perm[t];
+  spos[t] = make_int4((pos[3 * (size_t)i] - x0) & (CSO_BOX - 1), pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2],
+                      (int)i);
+  sid[t] = ids[i];
 }
 
 __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_t b2) {
@@ -779,7 +792,8 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
   size_t mark = ws.off;
   uint32_t* key = ws.get<uint32_t>(n);
   uint32_t* rank = ws.get<uint32_t>(n);
-  if (!key || !rank) {
+  uint32_t* perm = ws.get<uint32_t>(n);
+  if (!key || !rank || !perm) {
     cso_set_error("workspace exhausted in binning");
     return CSO_ERR_BUDGET;
   }
@@ -790,7 +804,8 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
   }
   CSO_TRY(scan_u32(start, ncell + 1, nullptr, ws, st));
   if (n > 0) {
-    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g.x0, key, rank, start, spos, sid, inv);
+    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(n, key, rank, start, perm, inv);
+    k_cell_gather<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g.x0, perm, spos, sid);
     CSO_CUDA(cudaGetLastError());
   }
   ws.off = mark;
