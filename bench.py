@@ -382,6 +382,10 @@ def main():
                    "sample": "medium recipe, %d seeded periodic boxes of side 64 l_mean (one per core, %d particles "
                              "in all) in parallel processes, %.1f s wall" % (cores, n_all, wall_all)}
 
+    # measured pipe rates of this GPU (integer ALU, IMAD, shared-memory
+    # broadcast), the denominators of the pair-kernel roofline
+    pipes = cso.cso_probe_peaks(local) if rank == 0 else None
+
     pos, ids, meta = make_workload(args.workload, rank)
     n = len(pos)
     params = cso.cso_params_default(meta["u"])
@@ -498,15 +502,17 @@ def main():
     # dominant kernel: the density pair loop, bounded by the integer ALU
     dens_ms = stages.get("density")
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops / s, in T/s
+    derived_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops / s, in T/s
+    alu_peak = pipes["alu_tops"] if pipes else derived_peak
     roof = None
     if dens_ms:
         achieved = stats["pairs_b"] * OPS_PER_PAIR / (dens_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "k_density", "achieved": achieved, "peak": alu_peak,
                 "unit": "Tops/s", "frac": achieved / alu_peak,
                 "traffic": DENSITY_DRAM_BYTES.get(args.workload),
-                "peak_source": "derived: 152 SMs x 128 int32 lanes x %.0f MHz (max SM clock, %s peaks file)"
-                               % (sm_mhz, peak_src),
+                "peak_source": ("measured: integer add/xor lane-op chains on this GPU (cso_probe_peaks)" if pipes
+                                else "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_mhz),
+                "peak_derived": derived_peak, "pipes": pipes,
                 "algorithmic": "%d pairs within b x %d int ops" % (stats["pairs_b"], OPS_PER_PAIR)}
     line = {
         "metric": "CompaSO particles/s (whole hot path: density, L0, L1, L2, catalogue)",

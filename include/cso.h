@@ -251,6 +251,15 @@ int cso_last_stats(cso_ctx* ctx, int64_t* out, int cap);
 /* One-line description of the last error of this thread. */
 const char* cso_last_error(void);
 
+/* Measured peak rates of the pipes the pair kernels use, on `device`:
+ * out[0] integer add/xor lane-ops per second (Tops/s), out[1] integer
+ * multiply-add lane-ops per second (Tops/s), out[2] bytes per second
+ * delivered to lanes by 128-bit shared-memory loads that a whole warp reads
+ * from one address (TB/s).  Each is one timed launch of independent
+ * dependency chains over 8 blocks of 256 threads per SM, after one untimed
+ * launch.  Allocates and frees a small device buffer; needs n >= 3. */
+int cso_probe_peaks(int device, double* out, int n);
+
 /* Sizes in bytes of the structs above as this library was compiled:
  * out[0..4] = sizeof cso_params, cso_halo, cso_input, cso_output, cso_radial
  * (so that a binding can check its own layouts).  Writes min(n, 5) entries

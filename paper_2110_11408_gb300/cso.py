@@ -136,6 +136,7 @@ def lib(build_if_missing=True):
                                        P(ctypes.c_double)]
         L.cso_clock.restype = ctypes.c_double
         L.cso_struct_sizes.argtypes = [P(ctypes.c_int64), ctypes.c_int]
+        L.cso_probe_peaks.argtypes = [ctypes.c_int, P(ctypes.c_double), ctypes.c_int]
         _lib = L
     return _lib
 
@@ -371,3 +372,11 @@ class Context:
 
     def stats(self):
         return cso_last_stats(self.h)
+
+
+def cso_probe_peaks(device=0):
+    """Measured pipe rates: integer add/xor and multiply-add (Tops/s), and
+    broadcast 128-bit shared-memory loads (TB/s delivered to lanes)."""
+    a = (ctypes.c_double * 3)()
+    _check(lib().cso_probe_peaks(int(device), a, 3), "cso_probe_peaks")
+    return {"alu_tops": a[0], "imad_tops": a[1], "lds_broadcast_tbs": a[2]}
