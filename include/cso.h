@@ -45,9 +45,11 @@ extern "C" {
 #define CSO_GRID_BITS 21
 
 /* context flags (cso_init) */
-#define CSO_FLAG_BATCHED 1u /* CompaSO levels run as one persistent size-binned launch */
+#define CSO_FLAG_BATCHED 1u /* CompaSO levels by group size: warp, 256- and 1024-thread blocks, 8-CTA clusters,
+                              largest first, on three concurrent streams */
 #define CSO_FLAG_TIMING 2u  /* record per-stage CUDA events (cso_stage_times) */
-#define CSO_FLAG_GRAPH 4u   /* replay the batched CompaSO launch sequence as a CUDA graph */
+/* value 4 is unused: the step is not captured as a CUDA graph (its launch
+ * sizes are read back from the device between stages) */
 #define CSO_FLAG_COUNT_PAIRS 8u /* count kernel pairs with d < b2 (cso_last_stats[6]); slows the density pass */
 #define CSO_FLAG_SELECT_STRESS 16u /* testing: tiny radius-search tiles so every select branch runs; same results */
 /* served path: number of worker slots (concurrent requests), 1..15; 0 = 4 */

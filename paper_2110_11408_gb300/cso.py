@@ -31,7 +31,6 @@ NO_GROUP = np.uint64(0xFFFFFFFFFFFFFFFF)
 
 FLAG_BATCHED = 1
 FLAG_TIMING = 2
-FLAG_GRAPH = 4
 FLAG_COUNT_PAIRS = 8
 FLAG_SELECT_STRESS = 16
 
