@@ -63,6 +63,11 @@ RADIAL_DTYPE = np.dtype([
 # fractions of the members enclosed by r_q (Table 1, r_XX_L2com)
 RADIAL_PERCENT = (25, 50, 75, 98)
 
+SHRINK_DTYPE = np.dtype([("centre", np.int64, 3), ("n", np.int64), ("R2", np.int64), ("iter", np.int64)])
+
+# the shrinking sphere stops below max(ceil(N / 100), SHRINK_N_MIN) members (Sec. 4)
+SHRINK_N_MIN = 700
+
 
 def build(force=False):
     """Compile the oracle with gcc (plain -O2, no tuning)."""
@@ -108,6 +113,9 @@ def lib():
                                  ctypes.c_int64, ctypes.c_double, ctypes.c_void_p]
         assert L.orc_sizeof_halo() == ctypes.sizeof(OrcHalo) == HALO_DTYPE.itemsize
         assert L.orc_sizeof_radial() == RADIAL_DTYPE.itemsize
+        L.orc_shrink_sphere.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+        assert L.orc_sizeof_shrink() == SHRINK_DTYPE.itemsize
         assert L.orc_sizeof_params() == ctypes.sizeof(OrcParams)
         assert L.orc_stats_count() == len(ST_NAMES)
         _lib = L
@@ -230,4 +238,20 @@ def radial(pos, l1, halos, u):
     rc = lib().orc_radial(_ptr(pos), _ptr(l1), pos.shape[0], _ptr(halos), halos.size, float(u), _ptr(out))
     if rc != 0:
         raise RuntimeError("oracle radial: a row has no members")
+    return out[:halos.size].copy()
+
+
+def shrink_sphere(pos, ids, l1, halos, n_min=SHRINK_N_MIN):
+    """Shrinking-sphere centre of every catalogue row (Sec. 4): from the L1
+    nucleus and radius, 5% smaller spheres about the rounded centre of mass
+    until fewer than max(ceil(N / 100), n_min) members remain."""
+    pos = _pos(pos)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    l1 = np.ascontiguousarray(l1, dtype=np.uint64)
+    halos = np.ascontiguousarray(halos, dtype=HALO_DTYPE)
+    out = np.zeros(max(halos.size, 1), SHRINK_DTYPE)
+    rc = lib().orc_shrink_sphere(_ptr(pos), _ptr(ids), _ptr(l1), pos.shape[0], _ptr(halos), halos.size,
+                                 int(n_min), _ptr(out))
+    if rc != 0:
+        raise RuntimeError("oracle shrink_sphere: a row's nucleus is not among its members")
     return out[:halos.size].copy()

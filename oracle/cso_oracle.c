@@ -766,3 +766,86 @@ int orc_radial(const int32_t* pos, const uint64_t* l1, int64_t n, const orc_halo
 }
 
 int orc_sizeof_radial(void) { return (int)sizeof(orc_radial_t); }
+
+/* ------------------------------------------------------------------------- */
+/* shrinking-sphere centre of catalogue rows (Sec. 4, Power et al. 2003)      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t centre[3]; /* final centre (grid point)                                */
+  int64_t n;         /* members inside the last sphere tested (below the stop)   */
+  int64_t R2;        /* squared radius of that sphere                            */
+  int64_t iter;      /* centre-of-mass steps taken                               */
+} orc_shrink_t;
+
+/* The centre of the CompaSO sphere followed inwards: starting at the L1
+ * nucleus with the L1 radius, the members inside the current sphere
+ * (d < R2) give a centre of mass, rounded to the nearest grid point, and the
+ * radius shrinks by 5% (R2 <- floor(R2 * 9025 / 10000), exact); this repeats
+ * while the sphere holds at least max(ceil(N / 100), n_min) members, N the
+ * halo's members (Sec. 4 stops at 1% of the particles or about 700).  Members
+ * are the particles whose L1 label is the row's nucleus id.  Returns 0, or -1
+ * if a row's nucleus is not among its members. */
+int orc_shrink_sphere(const int32_t* pos, const uint64_t* ids, const uint64_t* l1, int64_t n,
+                      const orc_halo* rows, int64_t nrows, int64_t n_min, orc_shrink_t* out) {
+  kv_t* byl = (kv_t*)malloc(sizeof(kv_t) * (size_t)(n > 0 ? n : 1));
+  int rc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    byl[i].key = (int64_t)l1[i];
+    byl[i].idx = i;
+  }
+  qsort(byl, (size_t)n, sizeof(kv_t), cmp_kv_key);
+  for (int64_t r = 0; r < nrows && rc == 0; ++r) {
+    const orc_halo* h = &rows[r];
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) / 2;
+      if ((uint64_t)byl[mid].key < h->nucleus_id) lo = mid + 1;
+      else hi = mid;
+    }
+    int64_t end = lo;
+    while (end < n && (uint64_t)byl[end].key == h->nucleus_id) ++end;
+    const int64_t N = end - lo;
+    int32_t c[3] = {0, 0, 0};
+    int found = 0;
+    for (int64_t t = lo; t < end; ++t)
+      if (ids[byl[t].idx] == h->nucleus_id) {
+        memcpy(c, pos + 3 * byl[t].idx, sizeof(c));
+        found = 1;
+      }
+    if (!found) {
+      rc = -1;
+      break;
+    }
+    const int64_t stop = (N + 99) / 100 > n_min ? (N + 99) / 100 : n_min;
+    int64_t R2 = h->R2, iter = 0, m = 0;
+    for (;;) {
+      int64_t sum[3] = {0, 0, 0};
+      m = 0;
+      for (int64_t t = lo; t < end; ++t) {
+        const int32_t* q = pos + 3 * byl[t].idx;
+        if (dist2(q, c) >= R2) continue;
+        ++m;
+        for (int a = 0; a < 3; ++a) sum[a] += mi(q[a], c[a]);
+      }
+      if (m < stop) break;
+      for (int a = 0; a < 3; ++a) {
+        double f = (double)c[a] + (double)sum[a] / (double)m;
+        if (f < 0) f += (double)ORC_BOX;
+        if (f >= (double)ORC_BOX) f -= (double)ORC_BOX;
+        c[a] = (int32_t)(llround(f) & (ORC_BOX - 1));
+      }
+      R2 = R2 * 9025 / 10000;
+      ++iter;
+    }
+    orc_shrink_t* o = &out[r];
+    for (int a = 0; a < 3; ++a) o->centre[a] = c[a];
+    o->n = m;
+    o->R2 = R2;
+    o->iter = iter;
+  }
+  free(byl);
+  return rc;
+}
+
+int orc_sizeof_shrink(void) { return (int)sizeof(orc_shrink_t); }
