@@ -135,7 +135,14 @@ typedef struct cso_input {
  *           as n_a^2 d_b > n_b^2 d_a; equal values keep the smaller radius);
  *   r_q = sqrt(d_q) / u and r_vmax = sqrt(vmax_d2) / u in l_mean units;
  *   vmax = sqrt(vmax_n / r_vmax) in units of sqrt(G m_particle / l_mean)
- *           (0 when every member sits on the centre). */
+ *           (0 when every member sits on the centre).
+ * The shrinking-sphere centre (Sec. 4; Power et al. 2003): from the L1
+ * nucleus with the L1 radius, the members inside the sphere (d < R2) give a
+ * centre of mass, rounded to the nearest grid point, and the radius shrinks
+ * by 5% (R2 <- floor(R2 * 9025 / 10000)); this repeats while the sphere holds
+ * at least max(ceil(N / 100), 700) members.  ss_centre is the final centre,
+ * ss_n and ss_R2 the member count and squared radius of the last sphere
+ * tested (the one below the stop count), ss_iter the steps taken. */
 typedef struct cso_radial {
   int64_t centre[3];
   int64_t d_q[4];
@@ -144,6 +151,10 @@ typedef struct cso_radial {
   int64_t vmax_d2;
   double vmax;
   double r_vmax;
+  int64_t ss_centre[3];
+  int64_t ss_n;
+  int64_t ss_R2;
+  int64_t ss_iter;
 } cso_radial;
 
 /* Outputs, caller-allocated, length n in input order (NULL = not wanted);

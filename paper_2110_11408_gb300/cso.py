@@ -80,7 +80,11 @@ assert HALO_DTYPE.itemsize == ctypes.sizeof(CsoHalo)
 RADIAL_DTYPE = np.dtype([
     ("centre", np.int64, 3), ("d_q", np.int64, 4), ("r_q", np.float64, 4), ("vmax_n", np.int64),
     ("vmax_d2", np.int64), ("vmax", np.float64), ("r_vmax", np.float64),
+    ("ss_centre", np.int64, 3), ("ss_n", np.int64), ("ss_R2", np.int64), ("ss_iter", np.int64),
 ])
+
+# the shrinking sphere stops below max(ceil(N / 100), SHRINK_N_MIN) members
+SHRINK_N_MIN = 700
 
 
 class CsoInput(ctypes.Structure):

@@ -607,7 +607,8 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
       S.mark("radial");
       ALLOC(cso_radial, r1, H1);
       rad = r1;
-      CSO_TRY(radial_run(seg2, ehal2, epos2, na, rows, H1, gi.x0, p->l_mean_grid, rad, c->pinned, ws, st));
+      CSO_TRY(radial_run(seg2, ehal2, epos2, na, rows, H1, gi.x0, p->l_mean_grid, hnuc, epos, rad, c->pinned, ws,
+                         st));
       S.mark("catalogue");
     }
     ALLOC(uint32_t, kscan, H1 + 1);

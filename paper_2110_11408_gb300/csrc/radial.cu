@@ -132,10 +132,99 @@ __global__ void __launch_bounds__(RAD_NT) k_radial_stats(const uint64_t* __restr
   r.vmax = bn > 0 ? sqrt((double)bn / r.r_vmax) : 0.0;
 }
 
+// Shrinking-sphere centre, a block per halo: every step is one pass over the
+// halo's members (count and summed minimum-image offsets of those inside the
+// sphere, reduced over the block in one round), then thread 0 moves the
+// centre to the rounded centre of mass and shrinks the radius, or stops.  The
+// sums are exact integers, so the reduction order is free.  Haloes of at
+// least SS_BIG members (the ones that take many steps over many members) run
+// on 1024-thread blocks, the rest on 256-thread blocks; each launch skips the
+// other's haloes.
+constexpr long long SS_N_MIN = 700;
+constexpr long long SS_BIG = 16384;
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_shrink_sphere(const int4* __restrict__ epos, const uint32_t* __restrict__ seg,
+                                                      const int4* __restrict__ nuc_pos,
+                                                      const uint32_t* __restrict__ hnuc,
+                                                      const cso_halo* __restrict__ rows, int x0,
+                                                      cso_radial* __restrict__ out) {
+  __shared__ long long sh[NT / 32][4];
+  __shared__ int sc[3];
+  __shared__ long long sR2, sm, siter;
+  __shared__ int sgo;
+  const int h = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t b = seg[h];
+  const long long N = seg[h + 1] - b;
+  if ((N >= SS_BIG) != (NT == 1024)) return;
+  const long long stop = (N + 99) / 100 > SS_N_MIN ? (N + 99) / 100 : SS_N_MIN;
+  if (threadIdx.x == 0) {
+    const int4 p = nuc_pos[hnuc[h]];
+    sc[0] = p.x;
+    sc[1] = p.y;
+    sc[2] = p.z;
+    sR2 = rows[h].R2;
+    siter = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    const int cx = sc[0], cy = sc[1], cz = sc[2];
+    const long long R2 = sR2;
+    long long v[4] = {0, 0, 0, 0};  // count, summed dx, dy, dz
+    for (long long j = threadIdx.x; j < N; j += blockDim.x) {
+      const int4 q = epos[b + j];
+      const long long dx = min_image(q.x - cx), dy = min_image(q.y - cy), dz = min_image(q.z - cz);
+      if (dx * dx + dy * dy + dz * dz >= R2) continue;
+      v[0] += 1;
+      v[1] += dx;
+      v[2] += dy;
+      v[3] += dz;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+      for (int k = 0; k < 4; ++k) sh[w][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long t[4] = {0, 0, 0, 0};
+      for (int x = 0; x < (int)(blockDim.x >> 5); ++x)
+        for (int k = 0; k < 4; ++k) t[k] += sh[x][k];
+      const long long m = t[0];
+      sm = m;
+      if (m < stop) {
+        sgo = 0;
+      } else {
+        for (int a = 0; a < 3; ++a) {
+          double f = (double)sc[a] + (double)t[a + 1] / (double)m;
+          if (f < 0) f += (double)CSO_BOX;
+          if (f >= (double)CSO_BOX) f -= (double)CSO_BOX;
+          sc[a] = (int)(llround(f) & (CSO_BOX - 1));
+        }
+        sR2 = R2 * 9025 / 10000;
+        ++siter;
+        sgo = 1;
+      }
+    }
+    __syncthreads();
+    if (!sgo) break;
+  }
+  if (threadIdx.x == 0) {
+    cso_radial& r = out[h];
+    r.ss_centre[0] = (sc[0] + x0) & (CSO_BOX - 1);
+    r.ss_centre[1] = sc[1];
+    r.ss_centre[2] = sc[2];
+    r.ss_n = sm;
+    r.ss_R2 = sR2;
+    r.ss_iter = siter;
+  }
+}
+
 }  // namespace
 
 int radial_run(const uint32_t* seg, const uint32_t* ehal, const int4* epos, long long na, const cso_halo* rows,
-               int H, int x0, double u, cso_radial* out, void* pinned, Workspace& ws, cudaStream_t st) {
+               int H, int x0, double u, const uint32_t* hnuc, const int4* nuc_pos, cso_radial* out, void* pinned,
+               Workspace& ws, cudaStream_t st) {
   if (H <= 0) return CSO_OK;
   const size_t mark = ws.off;
   int4* cen = ws.get<int4>(H);
@@ -186,6 +275,8 @@ int radial_run(const uint32_t* seg, const uint32_t* ehal, const int4* epos, long
     }
   }
   k_radial_stats<<<CL(H), RAD_NT, 0, st>>>(sorted, dmask, seg, u, out);
+  k_shrink_sphere<1024><<<CL(H), 1024, 0, st>>>(epos, seg, nuc_pos, hnuc, rows, x0, out);
+  k_shrink_sphere<256><<<CL(H), 256, 0, st>>>(epos, seg, nuc_pos, hnuc, rows, x0, out);
   CSO_CUDA(cudaGetLastError());
   ws.off = mark;
   return CSO_OK;

@@ -59,7 +59,7 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(cso.CsoHalo) == 8 * 19
     assert ctypes.sizeof(cso.CsoInput) == 8 + 8 + 8 + 4 + 4 + 4 + 4 + 8
     assert ctypes.sizeof(cso.CsoOutput) == 8 * 5 + 8 + 8 + 4 + 4 + 8
-    assert cso.RADIAL_DTYPE.itemsize == 8 * 15
+    assert cso.RADIAL_DTYPE.itemsize == 8 * 21
     # the compiled library agrees on every layout
     sizes = (ctypes.c_int64 * 5)()
     assert cso.lib().cso_struct_sizes(sizes, 5) == 5

@@ -211,11 +211,17 @@ def test_medium_box_sampled_parity(ctx):
         np.testing.assert_allclose(mine["com"], halos["com"], rtol=1e-9, atol=1e-9 * BOX)
         # radial statistics of the same rows, from the oracle's own labels
         sel = np.isin(g["halos"]["nucleus_id"], halos["nucleus_id"])
-        assert_same_radial(g["radial"][sel], O.radial(pos[m], l1, halos, meta["u"]))
+        assert_same_radial(g["radial"][sel], O.radial(pos[m], l1, halos, meta["u"]),
+                           O.shrink_sphere(pos[m], ids[m], l1, halos))
 
 
-def assert_same_radial(a, b):
-    assert len(a) == len(b)
+def assert_same_radial(a, b, ss):
+    assert len(a) == len(b) == len(ss)
+    for f, fo in (("ss_centre", "centre"), ("ss_n", "n"), ("ss_R2", "R2"), ("ss_iter", "iter")):
+        if not np.array_equal(a[f], ss[fo]):
+            bad = np.nonzero(np.any((a[f] != ss[fo]).reshape(len(a), -1), axis=1))[0]
+            raise AssertionError("shrinking sphere %s differs in %d of %d rows, first %s: gpu %s oracle %s"
+                                 % (f, bad.size, len(a), bad[:3], a[f][bad[:3]], ss[fo][bad[:3]]))
     for f in O.RADIAL_DTYPE.names:
         if not np.array_equal(a[f], b[f]):
             bad = np.nonzero(np.any((a[f] != b[f]).reshape(len(a), -1), axis=1))[0]
@@ -231,8 +237,10 @@ def test_radial_statistics_tiny_box(ctx):
     g = ctx.find_groups(pos, ids, pg, on_device=True, radial=True)
     o = O.find_groups(pos, ids, po)
     assert_same(g, o)
-    assert_same_radial(g["radial"], O.radial(pos, o["l1"], o["halos"], U64))
+    assert_same_radial(g["radial"], O.radial(pos, o["l1"], o["halos"], U64),
+                       O.shrink_sphere(pos, ids, o["l1"], o["halos"]))
     assert (o["halos"]["n_l2"] == 0).any() and (o["halos"]["n_l2"] > 0).any()
+    assert (g["radial"]["ss_iter"] > 0).any()
     h = ctx.find_groups(pos, ids, pg, on_device=False, radial=True)
     assert np.array_equal(h["radial"], g["radial"])
 
@@ -244,7 +252,8 @@ def test_radial_statistics_across_periodic_corner(ctx, seed):
     g = ctx.find_groups(pos, ids, pg, radial=True)
     o = O.find_groups(pos, ids, po)
     assert_same(g, o)
-    assert_same_radial(g["radial"], O.radial(pos, o["l1"], o["halos"], U64))
+    assert_same_radial(g["radial"], O.radial(pos, o["l1"], o["halos"], U64),
+                       O.shrink_sphere(pos, ids, o["l1"], o["halos"], n_min=cso.SHRINK_N_MIN))
 
 
 def test_radial_rejected_for_slab_requests(ctx):
