@@ -326,7 +326,7 @@ __global__ void k_dense_list(const uint32_t* __restrict__ pos_in_list, const int
   if (s < n && parent[s] >= 0) didx[pos_in_list[s]] = s;
 }
 
-// Round one (in the spirit of Afforest, Sutton et al. 2018): each dense
+// Pass one (in the spirit of Afforest, Sutton et al. 2018): each dense
 // particle tests the W = 32 slots after it in its cell, cyclically, so every
 // pair of a cell of up to 33 particles is tested and a big cell is joined by
 // a band of links around it.  The band joins almost every dense particle of
@@ -451,7 +451,7 @@ __global__ void k_cell_list(const uint32_t* __restrict__ head_scan, const int* _
 }
 
 // Every cell that holds dense particles has a main tree: the tree of its
-// first dense particle after round one, kept at slot start[c] of a
+// first dense particle after pass one, kept at slot start[c] of a
 // per-particle array (the first slot of every non-empty cell is its own) so
 // the summary costs n entries instead of one per cell of the sparse table;
 // CELL_EMPTY marks cells without dense particles.  A dense particle outside
@@ -516,7 +516,7 @@ __global__ void k_straggler_list(const uint32_t* __restrict__ sscan, const int* 
   if (sscan[i + 1] != sscan[i]) slist[sscan[i]] = didx[i];
 }
 
-// Round two, main trees as units: for every cell with dense particles and
+// Pass two, main trees as units: for every cell with dense particles and
 // each of its 13 forward neighbours (every adjacent pair of cells once), the
 // two main trees are joined if any pair of their members links.  A warp
 // holds the cell, 32 slots at a time, streams the neighbour through shared
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(256) k_fof_cells(CellGrid g, const int4* __res
     fof_cell_pairs(g, spos, clist[wi], lfof2, parent, cell_root, strag, tile[w], tmain[w], tileA[w], hit[w], lane);
 }
 
-// Round three, the stragglers one by one (a list of them): against every neighbour cell in
+// Pass three, the stragglers one by one (a list of them): against every neighbour cell in
 // l_FoF reach (its own included), the first link into the cell's main tree
 // (skipped when that tree is already the straggler's) and every link to a
 // later straggler (each straggler pair once).  Cells out of reach of the
@@ -863,7 +863,7 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
   CSO_TRY(scan_u32(head, n, head + n, ws, st));
   k_cell_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(head, didx, nd, clist);
   const uint32_t* ncl = head + n;
-  // round one: bands inside cells; main trees and stragglers
+  // pass one: bands inside cells; main trees and stragglers
   k_fof_sample<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, didx, nd, lfof2, parent);
   k_fof_compress<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n);
   k_cell_root_init<<<CL(cdiv(n, 256)), 256, 0, st>>>(cell_root, n);
@@ -872,7 +872,7 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
   CSO_TRY(scan_u32(sflag, n, sflag + n, ws, st));
   k_straggler_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(sflag, didx, nd, slist);
   k_straggler_ranges<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, slist, sflag + n, srange);
-  // round two: main trees of adjacent cells; round three: stragglers
+  // pass two: main trees of adjacent cells; pass three: stragglers
   k_fof_cells<<<CL(152 * 8), 256, 0, st>>>(g, spos, clist, ncl, lfof2, parent, cell_root, strag);
   k_fof_stragglers<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, slist, sflag + n, lfof2, parent, cell_root, strag,
                                                      srange);
