@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(RAD_NT) k_radial_stats(const uint64_t* __restr
 
 // Shrinking-sphere centre, a block per halo: every step is one pass over the
 // halo's members (count and summed minimum-image offsets of those inside the
-// sphere, reduced over the block in one round), then thread 0 moves the
+// sphere, reduced over the block in one step), then thread 0 moves the
 // centre to the rounded centre of mass and shrinks the radius, or stops.  The
 // sums are exact integers, so the reduction order is free.  Haloes of at
 // least SS_BIG members (the ones that take many steps over many members) run
