@@ -72,3 +72,10 @@ def test_cosmology_scaling_matches_oracle():
         p = cso.cso_params_cosmology(cso.cso_params_default(8192), om, z)
         ref = O.cosmology(om, z)
         assert (p.delta_L0, p.delta_L1, p.delta_L2, p.l_fof) == pytest.approx(ref, rel=1e-12)
+
+
+def test_probe_rejects_a_short_result_buffer():
+    # argument checks come before any device call, so this runs without a GPU
+    out = (ctypes.c_double * 2)()
+    assert cso.lib().cso_probe_peaks(0, out, 2) == cso.CSO_ERR_ARG
+    assert b"3 results" in cso.lib().cso_last_error()
