@@ -1,14 +1,18 @@
-// The plain pipeline: one box, all stages on the context's stream.
+// The pipeline of one box, stage by stage on the context's stream (the
+// batched schedule adds two side streams inside the level stages):
 //
 //   bin      counting sort of particles into the dense cell table
 //   density  Sigma per particle (Eq. 1)
 //   fof      L0 groups over dense particles (Sec. 2.2.1)
 //   gather   dense particles sorted by (L0 group, Sigma desc, id asc)
-//   level1   CompaSO L1, block per L0 group (steps 1-4; the local-peak test
-//            of step 2 runs inside, only for eligible candidates)
+//   level1   CompaSO L1 per L0 group (steps 1-4; the local-peak test of
+//            step 2 runs inside, only for eligible candidates): a block per
+//            group, or by size a warp, block or thread-block cluster
 //   prep2    members of each L1 halo in key order and their L1 labels
-//   level2   CompaSO L2, block per L1 halo
-//   output   labels in input order, per-halo statistics, catalogue
+//   level2   CompaSO L2 per L1 halo, scheduled as level1
+//   halos    per-halo statistics and the catalogue (optionally the radial
+//            statistics and the shrinking-sphere centre)
+//   output   labels and kernel sums in input order
 #include <string.h>
 
 #include "cells.cuh"
