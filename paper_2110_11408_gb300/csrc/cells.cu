@@ -1,4 +1,4 @@
-// Cell binning, kernel density, L0 friends-of-friends and the local-peak test.
+// Cell binning, kernel density and L0 friends-of-friends.
 //
 // Particles are binned into nc^3 cells of side 2^21/nc >= b (a counting sort
 // into a dense cell table, x fastest), so every neighbour within b of a
