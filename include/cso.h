@@ -231,7 +231,7 @@ void cso_free(cso_ctx* ctx);
 
 /* Autotuner of the batched schedule (CSO_FLAG_BATCHED): runs the request
  * under each candidate pair of size bins -- groups above `giant` members on
- * 8-CTA thread-block clusters (16384, 65536, 262144), groups of at most
+ * 8-CTA thread-block clusters (4096, 8192, 16384, 65536, 262144), groups of at most
  * `small` members one per warp (32, 64); groups above max(giant / 16, 512)
  * run on 1024-thread blocks and the rest on 256-thread blocks -- times the
  * CompaSO levels, and keeps the fastest pair in the context for every later

@@ -235,14 +235,14 @@ extern "C" int cso_set_schedule(cso_ctx* c, int32_t giant, int32_t small) {
 extern "C" int cso_autotune(cso_ctx* c, const cso_input* in, const cso_params* p, cso_output* out,
                             int32_t* giant, int32_t* small) {
   if (!c) return CSO_ERR_ARG;
-  static const int giants[] = {16384, 65536, 262144};
+  static const int giants[] = {4096, 8192, 16384, 65536, 262144};
   static const int smalls[] = {32, 64};
   const uint32_t saved = c->flags;
   c->flags |= CSO_FLAG_TIMING | CSO_FLAG_BATCHED;
   LevelSchedule best = c->sched;
   double best_t = 1e30;
   int rc = CSO_OK;
-  for (int gi = 0; gi < 3 && rc == CSO_OK; ++gi)
+  for (int gi = 0; gi < 5 && rc == CSO_OK; ++gi)
     for (int si = 0; si < 2 && rc == CSO_OK; ++si) {
       c->sched.giant = giants[gi];
       c->sched.small = smalls[si];
