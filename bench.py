@@ -502,7 +502,8 @@ def main():
     # dominant kernel: the density pair loop, bounded by the integer ALU
     dens_ms = stages.get("density")
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    derived_peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops / s, in T/s
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    derived_peak = n_sms * 128 * sm_mhz * 1e6 / 1e12  # int32 lane-ops / s, in T/s
     alu_peak = pipes["alu_tops"] if pipes else derived_peak
     roof = None
     if dens_ms:
@@ -511,7 +512,7 @@ def main():
                 "unit": "Tops/s", "frac": achieved / alu_peak,
                 "traffic": DENSITY_DRAM_BYTES.get(args.workload),
                 "peak_source": ("measured: integer add/xor lane-op chains on this GPU (cso_probe_peaks)" if pipes
-                                else "derived: 152 SMs x 128 int32 lanes x %.0f MHz" % sm_mhz),
+                                else "derived: %d SMs x 128 int32 lanes x %.0f MHz" % (n_sms, sm_mhz)),
                 "peak_derived": derived_peak, "pipes": pipes,
                 "algorithmic": "%d pairs within b x %d int ops" % (stats["pairs_b"], OPS_PER_PAIR)}
     line = {

@@ -36,7 +36,7 @@ extern "C" {
 #define CSO_ERR_ARG (-1)      /* bad parameters, positions outside [0, 2^21), n too large */
 #define CSO_ERR_BUDGET (-2)   /* the request can never fit the context's device-memory budget */
 #define CSO_ERR_CAPACITY (-3) /* halo_cap too small; n_halos holds the number needed */
-#define CSO_ERR_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define CSO_ERR_TIMEOUT (-4)  /* a bounded wait gave up (cso_poll with timeout_us > 0) */
 #define CSO_ERR_CUDA (-5)     /* a CUDA runtime call failed */
 #define CSO_EAGAIN (-6)       /* cso_submit: queued, not yet admitted (ticket is valid) */
 #define CSO_ERR_STATE (-7)    /* unknown ticket or call out of order */
@@ -216,7 +216,9 @@ int cso_submit(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_outpu
 
 /* Wait up to timeout_us (0 = just test, <0 = wait forever) for a ticket;
  * *done = 1 when its outputs are complete; returns the request's own status
- * once done (CSO_OK while still running).  CSO_ERR_STATE: unknown ticket. */
+ * once done.  While the request is still running: CSO_OK for timeout_us == 0,
+ * CSO_ERR_TIMEOUT when a positive timeout_us has passed (the ticket stays
+ * valid; poll again).  CSO_ERR_STATE: unknown ticket. */
 int cso_poll(cso_ctx* ctx, uint64_t ticket, int32_t* done, int32_t timeout_us);
 
 /* Host steady-clock times (seconds, the cso_clock() scale) at which a done
@@ -295,9 +297,13 @@ int cso_struct_sizes(int64_t* out, int n);
  * freed.  Limits: n <= CSO_STATIC_MAX_N and at most CSO_STATIC_MAX_CELLS
  * cells (boxes of up to 64 l_mean per side at the default b); larger requests
  * return CSO_ERR_ARG.  The first call on a device looks up the array's
- * device address, so make it before any stream capture.  All calls share
- * the one array: calls that overlap on the GPU (other threads, other
- * streams) race and must be serialised by the caller. */
+ * device address, so make it before any stream capture; the address is kept
+ * for the life of the process, so after a cudaDeviceReset (or any other
+ * teardown of the device's primary context) this entry point must not be
+ * called again in that process.  All calls share the one array and it keeps
+ * the last call's contents (each call clears what must start at zero): calls
+ * that overlap on the GPU (other threads, other streams) race and must be
+ * serialised by the caller. */
 #define CSO_STATIC_MAX_N (1 << 20)
 #define CSO_STATIC_MAX_CELLS (1 << 22)
 int cso_density_static(const int32_t* pos, int64_t n, const cso_params* p, int64_t* sigma, void* stream);

@@ -109,6 +109,10 @@ def lib():
         L.orc_find_groups.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, P(OrcParams),
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_int64, P(ctypes.c_int64), ctypes.c_void_p]
+        L.orc_halo_row.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+        L.orc_halo_row.restype = None
         L.orc_radial.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                  ctypes.c_int64, ctypes.c_double, ctypes.c_void_p]
         assert L.orc_sizeof_halo() == ctypes.sizeof(OrcHalo) == HALO_DTYPE.itemsize
@@ -226,6 +230,26 @@ def find_groups(pos, ids, p):
         raise RuntimeError("oracle failed: %d" % rc)
     return dict(sigma=sigma, l0=l0, l1=l1, l2=l2, halos=halos[:nh.value].copy(),
                 stats=dict(zip(ST_NAMES, st.tolist())))
+
+
+def halo_row(pos, ids, l0, u, nucleus, R2, members, slot2, l2_nuclei):
+    """One catalogue row of an L1 halo from its members (particle indices,
+    the nucleus among them), the L1 nucleus and squared radius, and the L2
+    assignment inside it: slot2[m] = ordinal of the L2 nucleus of member m
+    (-1: none), l2_nuclei = particle indices of the L2 nuclei in acceptance
+    order (densest first)."""
+    pos = _pos(pos)
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    l0 = np.ascontiguousarray(l0, dtype=np.uint64)
+    members = np.ascontiguousarray(members, dtype=np.int64)
+    slot2 = np.ascontiguousarray(slot2, dtype=np.int64)
+    l2_nuclei = np.ascontiguousarray(l2_nuclei, dtype=np.int64)
+    assert members.size == slot2.size and members.size > 0
+    assert slot2.max() < l2_nuclei.size
+    out = np.zeros(1, HALO_DTYPE)
+    lib().orc_halo_row(_ptr(pos), _ptr(ids), _ptr(l0), int(u), int(nucleus), int(R2), _ptr(members), members.size,
+                       _ptr(slot2), l2_nuclei.size, _ptr(l2_nuclei), _ptr(out))
+    return out[0]
 
 
 def radial(pos, l1, halos, u):

@@ -527,6 +527,46 @@ static void com_of(const int32_t* pos, const int32_t* nuc, const int64_t* mem, i
 
 static int cmp_desc_i64(const void* a, const void* b) { return -cmp_i64(a, b); }
 
+/* One catalogue row (Sec. 2.2.2 last paragraphs, Table 1) of an L1 halo.
+ * hmem[0..nh): the halo's members (particle indices; the nucleus pn among
+ * them), R2 its squared L1 radius; the L2 level inside it: slot2[m] is the
+ * ordinal of the L2 nucleus that member hmem[m] belongs to (-1: none), and
+ * l2nuc[0..n2) the L2 nuclei (particle indices) in the order they were
+ * accepted, densest first.  Fills:
+ *   N, R2, R_delta = sqrt(R2) / u, com (centre of mass of the members),
+ *   l0_id, n_l2 = n2, L2max = the first L2 nucleus with its member count
+ *   and centre of mass, l2_top5_N = the five largest L2 member counts in
+ *   descending order, zero-padded. */
+void orc_halo_row(const int32_t* pos, const uint64_t* ids, const uint64_t* l0, int64_t u, int64_t pn, int64_t R2,
+                  const int64_t* hmem, int64_t nh, const int64_t* slot2, int64_t n2, const int64_t* l2nuc,
+                  orc_halo* H) {
+  memset(H, 0, sizeof(*H));
+  H->nucleus_id = ids[pn];
+  H->N = nh;
+  H->R2 = R2;
+  H->R_delta = sqrt((double)R2) / (double)u;
+  com_of(pos, pos + 3 * pn, hmem, nh, H->com);
+  H->l0_id = l0[pn];
+  H->n_l2 = n2;
+  H->l2max_id = ORC_NONE;
+  int64_t* sizes = (int64_t*)calloc((size_t)(n2 > 0 ? n2 : 1), sizeof(int64_t));
+  for (int64_t m = 0; m < nh; ++m) if (slot2[m] >= 0) sizes[slot2[m]]++;
+  if (n2 > 0) {
+    /* L2max: the first L2 nucleus, i.e. the densest one */
+    int64_t pl = l2nuc[0];
+    H->l2max_id = ids[pl];
+    H->l2max_N = sizes[0];
+    int64_t* l2mem = (int64_t*)malloc(sizeof(int64_t) * (size_t)(sizes[0] > 0 ? sizes[0] : 1));
+    int64_t k2 = 0;
+    for (int64_t m = 0; m < nh; ++m) if (slot2[m] == 0) l2mem[k2++] = hmem[m];
+    com_of(pos, pos + 3 * pl, l2mem, k2, H->l2max_com);
+    free(l2mem);
+  }
+  qsort(sizes, (size_t)n2, sizeof(int64_t), cmp_desc_i64);
+  for (int k = 0; k < 5; ++k) H->l2_top5_N[k] = k < n2 ? sizes[k] : 0;
+  free(sizes);
+}
+
 /* CompaSO L1 inside every L0 group, then L2 inside every L1 halo
  * (Sec. 2.2.2), labels and per-halo statistics (Sec. 2.2.2 last paragraphs,
  * Table 1).  Catalogue rows are written for L1 haloes with N >= np_min_L1,
@@ -557,7 +597,7 @@ int orc_compaso(const int32_t* pos, const uint64_t* ids, const int64_t* sigma, c
   int64_t* slot2 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nd > 0 ? nd : 1));
   orc_nucleus* nuc2 = (orc_nucleus*)malloc(sizeof(orc_nucleus) * (size_t)(nd > 0 ? nd : 1));
   int64_t* hmem = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nd > 0 ? nd : 1));
-  int64_t* l2mem = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nd > 0 ? nd : 1));
+  int64_t* l2nuc = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nd > 0 ? nd : 1));
 
   int64_t cap_rows = 0, rows = 0;
   orc_halo* tmp = NULL;
@@ -594,31 +634,8 @@ int orc_compaso(const int32_t* pos, const uint64_t* ids, const int64_t* sigma, c
         cap_rows = cap_rows ? 2 * cap_rows : 1024;
         tmp = (orc_halo*)realloc(tmp, sizeof(orc_halo) * (size_t)cap_rows);
       }
-      orc_halo* H = tmp + rows++;
-      memset(H, 0, sizeof(*H));
-      int64_t pn = M[nuc[h].member];
-      H->nucleus_id = ids[pn];
-      H->N = nh;
-      H->R2 = nuc[h].R2;
-      H->R_delta = sqrt((double)nuc[h].R2) / (double)p->u;
-      com_of(pos, pos + 3 * pn, hmem, nh, H->com);
-      H->l0_id = l0[pn];
-      H->n_l2 = n2;
-      H->l2max_id = ORC_NONE;
-      int64_t* sizes = (int64_t*)calloc((size_t)(n2 > 0 ? n2 : 1), sizeof(int64_t));
-      for (int64_t m = 0; m < nh; ++m) if (slot2[m] >= 0) sizes[slot2[m]]++;
-      if (n2 > 0) {
-        /* L2max: the first L2 nucleus, i.e. the densest one */
-        int64_t pl = hmem[nuc2[0].member];
-        H->l2max_id = ids[pl];
-        H->l2max_N = sizes[0];
-        int64_t k2 = 0;
-        for (int64_t m = 0; m < nh; ++m) if (slot2[m] == 0) l2mem[k2++] = hmem[m];
-        com_of(pos, pos + 3 * pl, l2mem, k2, H->l2max_com);
-      }
-      qsort(sizes, (size_t)n2, sizeof(int64_t), cmp_desc_i64);
-      for (int k = 0; k < 5; ++k) H->l2_top5_N[k] = k < n2 ? sizes[k] : 0;
-      free(sizes);
+      for (int64_t q = 0; q < n2; ++q) l2nuc[q] = hmem[nuc2[q].member];
+      orc_halo_row(pos, ids, l0, p->u, M[nuc[h].member], nuc[h].R2, hmem, nh, slot2, n2, l2nuc, tmp + rows++);
     }
     a = b;
   }
@@ -639,7 +656,7 @@ int orc_compaso(const int32_t* pos, const uint64_t* ids, const int64_t* sigma, c
   else if (rows > 0) memcpy(halos, tmp, sizeof(orc_halo) * (size_t)rows);
   if (stats) for (int k = ORC_ST_L0_GROUPS; k < ORC_ST_COUNT; ++k) if (k != ORC_ST_DENSE) stats[k] = st[k];
 
-  free(tmp); free(dense); free(slot); free(nuc); free(slot2); free(nuc2); free(hmem); free(l2mem);
+  free(tmp); free(dense); free(slot); free(nuc); free(slot2); free(nuc2); free(hmem); free(l2nuc);
   grid_free(&g);
   return rc;
 }

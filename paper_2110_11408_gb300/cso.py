@@ -28,6 +28,9 @@ CSO_ERR_CUDA = -5
 CSO_EAGAIN = -6
 CSO_ERR_STATE = -7
 NO_GROUP = np.uint64(0xFFFFFFFFFFFFFFFF)
+# limits of cso_density_static (include/cso.h)
+CSO_STATIC_MAX_N = 1 << 20
+CSO_STATIC_MAX_CELLS = 1 << 22
 
 FLAG_BATCHED = 1
 FLAG_TIMING = 2

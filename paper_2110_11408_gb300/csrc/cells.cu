@@ -22,9 +22,10 @@ __global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, CellG
   }
   // table column from the grid x (whole box or window alike)
   int tc = g.colmap ? g.colmap[cell_coord(x, g.nc)] : cell_coord(x, g.nc);
-  if (tc < 0) {  // a window particle outside the window's columns
+  if (tc < 0) {  // a window particle outside the window's columns: filed under cell 0 like the rest
     atomicExch(bad, 2);
     tc = 0;
+    y = z = 0;
   }
   const uint32_t k = (uint32_t)grid_cell(g, cell_coord(z, g.nc), cell_coord(y, g.nc), tc);
   key[i] = k;
@@ -45,14 +46,24 @@ __global__ void k_cell_scatter(long long n, const uint32_t* __restrict__ key, co
   if (inv) inv[i] = dst;
 }
 
-__global__ void k_cell_gather(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n, int x0,
-                              const uint32_t* __restrict__ perm, int4* __restrict__ spos,
+// A particle that k_cell_count rejected (outside the box, or outside a
+// window's columns) was filed under table cell 0; it is stored at that cell's
+// low corner so that every later kernel derives an in-range cell from it.  The
+// request still fails (the bad flag), but no kernel indexes past the table.
+__global__ void k_cell_gather(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n,
+                              CellGrid g, const uint32_t* __restrict__ perm, int4* __restrict__ spos,
                               uint64_t* __restrict__ sid) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const uint32_t i = perm[t];
-  spos[t] = make_int4((pos[3 * (size_t)i] - x0) & (CSO_BOX - 1), pos[3 * (size_t)i + 1], pos[3 * (size_t)i + 2],
-                      (int)i);
+  int x = pos[3 * (size_t)i], y = pos[3 * (size_t)i + 1], z = pos[3 * (size_t)i + 2];
+  const bool out = (unsigned)x >= (unsigned)CSO_BOX || (unsigned)y >= (unsigned)CSO_BOX ||
+                   (unsigned)z >= (unsigned)CSO_BOX || (g.colmap && g.colmap[cell_coord(x, g.nc)] < 0);
+  if (out) {
+    x = g.colmap ? cell_lo(g.cols[0], g.nc) : 0;
+    y = z = 0;
+  }
+  spos[t] = make_int4((x - g.x0) & (CSO_BOX - 1), y, z, (int)i);
   sid[t] = ids[i];
 }
 
@@ -805,7 +816,7 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
   CSO_TRY(scan_u32(start, ncell + 1, nullptr, ws, st));
   if (n > 0) {
     k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(n, key, rank, start, perm, inv);
-    k_cell_gather<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g.x0, perm, spos, sid);
+    k_cell_gather<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g, perm, spos, sid);
     CSO_CUDA(cudaGetLastError());
   }
   ws.off = mark;
@@ -873,7 +884,7 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
   k_straggler_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(sflag, didx, nd, slist);
   k_straggler_ranges<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, slist, sflag + n, srange);
   // pass two: main trees of adjacent cells; pass three: stragglers
-  k_fof_cells<<<CL(152 * 8), 256, 0, st>>>(g, spos, clist, ncl, lfof2, parent, cell_root, strag);
+  k_fof_cells<<<CL(cso_sm_count() * 8), 256, 0, st>>>(g, spos, clist, ncl, lfof2, parent, cell_root, strag);
   k_fof_stragglers<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, slist, sflag + n, lfof2, parent, cell_root, strag,
                                                      srange);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));

@@ -29,6 +29,9 @@ void cso_set_error(const char* fmt, ...);
 
 static inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
+// streaming multiprocessors of the current device (read once per device)
+int cso_sm_count();
+
 // every kernel launch of the library passes its grid size through CL(), which
 // counts the calling thread's launches for cso_last_stats
 extern thread_local long long g_cso_launches;

@@ -257,7 +257,13 @@ extern "C" int cso_poll(cso_ctx* c, uint64_t ticket, int32_t* done, int32_t time
     if (timeout_us < 0) S.cv_done.wait(lock, pred);
     else S.cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), pred);
   }
-  if (!r->done) return CSO_OK;
+  if (!r->done) {
+    if (timeout_us > 0) {
+      cso_set_error("ticket %llu not done after %d us", (unsigned long long)ticket, (int)timeout_us);
+      return CSO_ERR_TIMEOUT;
+    }
+    return CSO_OK;
+  }
   *done = 1;
   return r->status;
 }

@@ -55,6 +55,44 @@ def assert_same(g, o, n_sample_fp=None):
         np.testing.assert_allclose(H[f], Ho[f], rtol=1e-9, atol=1e-9 * BOX)
 
 
+_MEDIUM = {}
+
+
+def medium_box():
+    """The benchmark box (side 256, 16.8M particles), drawn once per session."""
+    if "box" not in _MEDIUM:
+        _MEDIUM["box"] = synth.medium()
+    return _MEDIUM["box"]
+
+
+def check_groups_against_oracle(g, pos, ids, po, pick, u, radial=True):
+    """L1/L2 labels and catalogue rows of the L0 groups `pick` of a GPU run
+    `g`, each recomputed by the oracle on exactly its own members, with
+    their kernel sums from the oracle on the full box."""
+    members = [np.nonzero(g["l0"] == gid)[0] for gid in pick]
+    # one oracle density pass over all members of all picked groups
+    sig_all = O.density_at(pos, po, np.concatenate(members))
+    cuts = np.cumsum([0] + [m.size for m in members])
+    for k, gid in enumerate(pick):
+        m = members[k]
+        sig = sig_all[cuts[k]:cuts[k + 1]]
+        assert np.array_equal(sig, g["sigma"][m])
+        l1, l2, halos, _ = O.compaso(pos[m], ids[m], sig, g["l0"][m], po)
+        assert np.array_equal(l1, g["l1"][m]), "L1 of group %d (%d members)" % (gid, m.size)
+        assert np.array_equal(l2, g["l2"][m]), "L2 of group %d (%d members)" % (gid, m.size)
+        sel = np.isin(g["halos"]["nucleus_id"], halos["nucleus_id"])
+        mine = g["halos"][sel]
+        assert len(mine) == len(halos)
+        for f in ("nucleus_id", "N", "R2", "l2max_id", "l2max_N", "l2_top5_N", "n_l2", "l0_id"):
+            assert np.array_equal(mine[f], halos[f]), f
+        for f in ("com", "l2max_com", "R_delta"):
+            np.testing.assert_allclose(mine[f], halos[f], rtol=1e-9, atol=1e-9 * BOX)
+        if radial:
+            # radial statistics of the same rows, from the oracle's own labels
+            assert_same_radial(g["radial"][sel], O.radial(pos[m], l1, halos, u),
+                               O.shrink_sphere(pos[m], ids[m], l1, halos))
+
+
 def run_both(ctx, pos, ids, u=U64, on_device=True, **kw):
     pg, po = both_params(u, **kw)
     g = ctx.find_groups(pos, ids, pg, on_device=on_device)
@@ -155,12 +193,32 @@ def test_edge_cases(ctx):
     assert_same(g, o)
 
 
-def test_rejects_positions_outside_grid(ctx):
+@pytest.mark.parametrize("bad", [[BOX, 0, 0], [0, BOX, 0], [0, 0, BOX], [5, -1, 7], [5, 7, -(1 << 30)],
+                                 [-(1 << 31), 1 << 30, 3]])
+def test_rejects_positions_outside_grid(ctx, bad):
+    """Any coordinate outside [0, 2^21) fails the request with CSO_ERR_ARG;
+    the rejected particle is binned and stored at cell 0, so every kernel of
+    the failed request still indexes inside its tables (patch particles
+    around it exercise density and FoF on the same run)."""
     p, _ = both_params(U64)
-    pos = np.array([[1, 2, 3], [BOX, 0, 0]], np.int32)
+    pos, ids, _ = synth.patch(extent=6.0, lo=-3.0, seed=2)
+    pos = np.concatenate([pos, np.array([bad], np.int32)])
+    ids = np.arange(len(pos), dtype=np.uint64)
     with pytest.raises(cso.CsoError) as e:
-        ctx.find_groups(pos, np.arange(2, dtype=np.uint64), p)
+        ctx.find_groups(pos, ids, p)
     assert e.value.rc == cso.CSO_ERR_ARG
+    # the context stays usable
+    g, o = run_both(ctx, pos[:-1], ids[:-1])
+    assert_same(g, o)
+
+
+def test_rejects_requests_of_2_31_particles(ctx):
+    """n >= 2^31 - 1 is refused before anything is read."""
+    p, _ = both_params(U64)
+    b = cso.Buffers(np.zeros((1, 3), np.int32), np.zeros(1, np.uint64), False)
+    b.cin.n = (1 << 31) - 1
+    assert cso.lib().cso_find_groups(ctx.h, b.cin, p, b.cout) == cso.CSO_ERR_ARG
+    assert "too large" in cso.cso_last_error()
 
 
 def test_capacity_error_reports_needed_rows(ctx):
@@ -178,7 +236,7 @@ def test_medium_box_sampled_parity(ctx):
     rows of 40 sampled L0 groups, each recomputed by the oracle on exactly
     its own members (their kernel sums from the oracle on the full box)."""
     from scipy.spatial import cKDTree
-    pos, ids, meta = synth.medium()
+    pos, ids, meta = medium_box()
     p, po = both_params(meta["u"], np_min_L1=1)
     g = ctx.find_groups(pos, ids, p, radial=True)
     rng = np.random.default_rng(3)
@@ -197,22 +255,7 @@ def test_medium_box_sampled_parity(ctx):
     groups, counts = np.unique(g["l0"][dense], return_counts=True)
     big = groups[counts >= 200]
     pick = np.concatenate([rng.choice(big, 20, replace=False), rng.choice(groups, 20, replace=False)])
-    for gid in pick:
-        m = np.nonzero(g["l0"] == gid)[0]
-        sig = O.density_at(pos, po, m)
-        assert np.array_equal(sig, g["sigma"][m])
-        l1, l2, halos, _ = O.compaso(pos[m], ids[m], sig, g["l0"][m], po)
-        assert np.array_equal(l1, g["l1"][m])
-        assert np.array_equal(l2, g["l2"][m])
-        mine = g["halos"][np.isin(g["halos"]["nucleus_id"], halos["nucleus_id"])]
-        assert len(mine) == len(halos)
-        for f in ("nucleus_id", "N", "R2", "l2max_id", "l2max_N", "l2_top5_N", "n_l2", "l0_id"):
-            assert np.array_equal(mine[f], halos[f]), f
-        np.testing.assert_allclose(mine["com"], halos["com"], rtol=1e-9, atol=1e-9 * BOX)
-        # radial statistics of the same rows, from the oracle's own labels
-        sel = np.isin(g["halos"]["nucleus_id"], halos["nucleus_id"])
-        assert_same_radial(g["radial"][sel], O.radial(pos[m], l1, halos, meta["u"]),
-                           O.shrink_sphere(pos[m], ids[m], l1, halos))
+    check_groups_against_oracle(g, pos, ids, po, pick, meta["u"])
 
 
 def assert_same_radial(a, b, ss):
@@ -302,10 +345,38 @@ def test_batched_select_stress():
         c.close()
 
 
+def test_batched_medium_box_giant_groups_parity():
+    """The batched schedule in the benchmark's tuned configuration (groups
+    above 65,536 members on 8-CTA clusters, above 4,096 on 1024-thread
+    blocks, up to 64 on warps) on the 16.8M-particle box, against the oracle:
+    the five largest L0 groups (cluster tier), four of the 1024-thread tier,
+    four of the 256-thread tier and four warp groups, each recomputed on its
+    own members."""
+    pos, ids, meta = medium_box()
+    p, po = both_params(meta["u"], np_min_L1=1)
+    c = cso.Context(0, flags=cso.FLAG_BATCHED)
+    try:
+        cso.cso_set_schedule(c.h, 65536, 64)
+        g = c.find_groups(pos, ids, p, radial=True)
+    finally:
+        c.close()
+    dense = g["l0"] != cso.NO_GROUP
+    groups, counts = np.unique(g["l0"][dense], return_counts=True)
+    order = np.argsort(-counts)
+    rng = np.random.default_rng(11)
+    giants = groups[order[:5]]
+    assert counts[order[0]] > 65536
+    tiers = [giants]
+    for lo, hi in ((4096, 65536), (64, 4096), (1, 64)):
+        sel = groups[(counts > lo) & (counts <= hi)]
+        tiers.append(rng.choice(sel, min(4, sel.size), replace=False))
+    check_groups_against_oracle(g, pos, ids, po, np.concatenate(tiers), meta["u"])
+
+
 def test_batched_equals_plain_on_medium_box(ctx, ctx_batched):
     """Same labels and catalogue, bit for bit, from both schedules on the
     16.8M-particle benchmark box."""
-    pos, ids, meta = synth.medium()
+    pos, ids, meta = medium_box()
     p = cso.cso_params_default(meta["u"])
     dpos = torch.from_numpy(pos).cuda()
     dids = torch.from_numpy(ids.view(np.int64)).cuda()

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2110_11408_gb300 import cso, synth
+from parity_util import assert_matches_oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -21,13 +22,17 @@ def boxes():
 
 @pytest.fixture(scope="module")
 def alone():
+    """Each box computed alone, and checked against the oracle, so that
+    "the same in the mix as alone" also means "the same as the oracle"."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     res = []
     with cso.Context(0) as ctx:
         for pos, ids, meta in boxes():
             p = cso.cso_params_default(meta["u"])
-            res.append(ctx.find_groups(pos, ids, p))
+            r = ctx.find_groups(pos, ids, p)
+            assert_matches_oracle(r, pos, ids, meta["u"])
+            res.append(r)
     return res
 
 
@@ -61,6 +66,8 @@ def test_budget_admits_one_request_at_a_time():
     data = [synth.tiny(seed=s) for s in (101, 102, 103)]
     with cso.Context(0) as ctx:
         ref = [ctx.find_groups(pos, ids, cso.cso_params_default(meta["u"])) for pos, ids, meta in data]
+    for r, (pos, ids, meta) in zip(ref, data):
+        assert_matches_oracle(r, pos, ids, meta["u"])
     with cso.Context(0, budget_bytes=(400 << 20), flags=cso.FLAG_SLOTS(3)) as ctx:
         bufs, tickets = [], []
         for pos, ids, meta in data:
@@ -103,3 +110,18 @@ def test_bad_request_fails_alone(alone):
         same(b_good.result(), alone[1])
         done, rc = ctx.wait(987654)
         assert rc == cso.CSO_ERR_STATE and not done
+
+
+def test_bounded_poll_times_out_then_completes():
+    """A positive timeout that passes before the request is done returns
+    CSO_ERR_TIMEOUT with done = 0; the ticket stays valid and completes."""
+    pos, ids, meta = synth.tiny(seed=104)
+    with cso.Context(0, flags=cso.FLAG_SLOTS(1)) as ctx:
+        b = cso.Buffers(pos, ids, False)
+        t = ctx.submit(b, cso.cso_params_default(meta["u"]))
+        done, rc = ctx.wait(t, timeout_us=1)
+        # a 262k-particle request takes milliseconds; 1 us cannot cover it
+        assert (not done and rc == cso.CSO_ERR_TIMEOUT) or (done and rc == cso.CSO_OK)
+        assert ctx.wait(t, timeout_us=0)[1] == cso.CSO_OK  # a plain test never times out
+        done, rc = ctx.wait(t)
+        assert done and rc == cso.CSO_OK

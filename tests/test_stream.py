@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2110_11408_gb300 import cso, synth
+from parity_util import assert_matches_oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -19,6 +20,8 @@ def box():
     p = cso.cso_params_default(meta["u"])
     with cso.Context(0) as ctx:
         whole = ctx.find_groups(pos, ids, p, halo_cap=len(pos) // 10)
+    # the whole-box result every slab stream is compared with is the oracle's
+    assert_matches_oracle(whole, pos, ids, meta["u"])
     return pos, ids, p, whole
 
 
@@ -80,6 +83,7 @@ def test_two_streams_and_whole_boxes_in_the_mix(box):
     pos2, ids2, meta2 = synth.tiny(seed=78)
     with cso.Context(0) as ctx:
         whole2 = ctx.find_groups(pos2, ids2, p, halo_cap=len(pos2) // 10)
+    assert_matches_oracle(whole2, pos2, ids2, meta2["u"])
     with cso.Context(0, flags=cso.FLAG_SLOTS(4)) as ctx:
         e1 = [BOX * k // 8 for k in range(9)]
         e2 = [BOX * k // 5 for k in range(6)]

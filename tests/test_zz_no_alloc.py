@@ -73,3 +73,21 @@ def test_static_density_rejects_oversized_requests(dev):
     fine = cso.cso_params_default(16384)  # box 128: 320^3 cells, beyond the table limit
     rc = L.cso_density_static(dummy.data_ptr(), 1, ctypes.byref(fine), out.data_ptr(), None)
     assert rc == cso.CSO_ERR_ARG and "cells exceed" in cso.cso_last_error()
+
+
+def test_static_density_at_its_documented_limits(dev):
+    """2^20 particles (the particle limit) in a box of 64 l_mean per side (the
+    largest cell table the limit admits at the default b): the scratch array
+    holds the cell table, the sorted copy and the binning scratch of the
+    largest request, and the sums equal the allocating path's."""
+    pos, ids, meta = synth.nfw_box(64, 0.5, 20, 20000, seed=41, n_total=1 << 20)
+    assert len(pos) == cso.CSO_STATIC_MAX_N
+    p = cso.cso_params_default(meta["u"])
+    with cso.Context(0) as ctx:
+        ref = ctx.find_groups(pos, ids, p)["sigma"]
+    dpos = torch.from_numpy(pos).to(dev)
+    for _ in range(2):
+        rc, out = static_density(dpos, p)
+        assert rc == cso.CSO_OK, cso.cso_last_error()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref)
