@@ -34,12 +34,28 @@ WORKLOADS = {
     "medium128": dict(desc="the medium recipe in a side-128 box: 2,097,152 particles (profiling size)"),
     "tiny": dict(desc="tiny box: side 64 l_mean, 262,144 particles, 50% background, 50% NFW haloes N in "
                       "[20, 2e4]"),
+    "batched": dict(desc="pre-formed groups: 4,000,000 particles in a side-256 box, group sizes with equal "
+                         "particles per log interval on [35, 2e6] plus one forced 2e6 giant, each an NFW host with "
+                         "0-5 NFW subhaloes (mass ratio 0.01-0.3), groups isolated (no background)"),
+    "batched_many": dict(desc="100,000 pre-formed groups of 35-45 particles (single NFW haloes), ~4.0M particles "
+                              "in a side-256 box"),
 }
 OPS_PER_PAIR = 11  # 3 sub, 3 mul, 2 add for d; compare; b2 - d; accumulate
 # DRAM bytes (read + write) of one k_density launch on the medium box, from
 # the single-pass ncu capture summarised in profiles/density_medium_dram.md;
 # valid for that kernel as it stands, and only for the medium workload
 DENSITY_DRAM_BYTES = {"medium": 3.25e9 + 135.21e6}
+
+
+def cell_table_bytes(u):
+    """Bytes of the dense cell table of a whole box of spacing u (cells of
+    side >= b = 0.4 u, uint32 offsets)."""
+    import math
+    b2 = round((0.4 * u) ** 2)
+    nc = int((1 << 21) / math.sqrt(b2))
+    while (1 << 42) < b2 * nc * nc:
+        nc -= 1
+    return 4 * (nc ** 3 + 1)
 
 
 def load_peaks():
@@ -149,6 +165,10 @@ def make_workload(name, seed_offset):
         return synth.tiny(seed=synth.SEED0 + 1000 * seed_offset)
     if name == "medium128":
         return synth.medium_sample(side=128, seed=synth.SEED0 + 11 + 1000 * seed_offset)
+    if name == "batched":
+        return synth.batched(seed=synth.SEED0 + 3 + 1000 * seed_offset)
+    if name == "batched_many":
+        return synth.batched_many(seed=synth.SEED0 + 4 + 1000 * seed_offset)
     raise SystemExit("unknown workload " + name)
 
 
@@ -521,8 +541,8 @@ def main():
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "n_particles": n,
-                   "schedule": primary, "autotuned_bins": tuned, "l2_flush": "working set > L2 (inputs 336 MB, "
-                   "cell table 1 GB)", "seed": meta["seed"]},
+                   "schedule": primary, "autotuned_bins": tuned, "l2_flush": "working set > L2 (inputs %.0f MB, cell table %.2f GB, L2 129 MB)"
+                   % (n * 20 / 1e6, cell_table_bytes(meta["u"]) / 1e9), "seed": meta["seed"]},
         "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all, "clocks": clocks, "served": served, "other_schedule": other,
         "radial": radial,

@@ -204,3 +204,133 @@ def lattice_ball(a, k_max, centre):
     g = g[(g * g).sum(1) <= k_max]
     pos = np.mod(np.asarray(centre, np.int64)[None, :] + a * g, BOX).astype(np.int32)
     return pos, np.arange(len(pos), dtype=np.uint64), dict(n=len(pos))
+
+
+# --------------------------------------------------------------------------
+# pre-formed groups (the batched workload)
+# --------------------------------------------------------------------------
+
+def group_sizes_particle_weighted(rng, nmin, nmax, total, giant=None):
+    """Group sizes with equal numbers of particles per logarithmic size
+    interval on [nmin, nmax] (dN/dN ~ N^-2), drawn until `total` particles
+    are used; `giant` (if given) is the first group.  The last group takes the
+    remainder if that is at least nmin (else the remainder is dropped)."""
+    sizes = [int(giant)] if giant else []
+    used = sum(sizes)
+    a, b = 1.0 / nmin, 1.0 / nmax
+    while used < total:
+        q = rng.random(4096)
+        for n in np.floor(1.0 / (a - q * (a - b))).astype(np.int64):
+            n = int(min(n, total - used))
+            if n < nmin:
+                return np.asarray(sizes, np.int64)
+            sizes.append(n)
+            used += n
+            if used >= total:
+                break
+    return np.asarray(sizes, np.int64)
+
+
+def _place_spheres(rng, radii, side):
+    """Centres (l_mean units) of non-overlapping spheres of the given radii in
+    a periodic box, placed largest first by rejection; candidates are checked
+    against the spheres registered in the hash cells their bounding box
+    covers."""
+    order = np.argsort(-radii, kind="stable")
+    h = max(2.0 * float(np.median(radii)), 1e-3)
+    nh = max(1, int(side // h))
+    h = side / nh
+    table = {}
+    cen = np.zeros((radii.size, 3))
+
+    def cells(c, r):
+        lo = np.floor((c - r) / h).astype(np.int64)
+        hi = np.floor((c + r) / h).astype(np.int64)
+        for x in range(lo[0], hi[0] + 1):
+            for y in range(lo[1], hi[1] + 1):
+                for z in range(lo[2], hi[2] + 1):
+                    yield (x % nh, y % nh, z % nh)
+
+    for i in order:
+        r = radii[i]
+        for _ in range(10000):
+            c = rng.random(3) * side
+            near = {j for key in cells(c, r) for j in table.get(key, ())}
+            if near:
+                js = np.fromiter(near, np.int64)
+                d = np.abs(cen[js] - c)
+                d = np.minimum(d, side - d)
+                if (np.einsum("ij,ij->i", d, d) < (radii[js] + r) ** 2).any():
+                    continue
+            break
+        else:
+            raise RuntimeError("cannot place group %d" % i)
+        cen[i] = c
+        for key in cells(c, r):
+            table.setdefault(key, []).append(i)
+    return cen
+
+
+def preformed_groups(side, sizes, max_subs, sub_ratio, c_range=(4.0, 12.0), sub_offset=(0.2, 0.9), margin=0.5,
+                     seed=0, min_sub=20):
+    """Isolated groups in a periodic box of `side` l_mean (no background).
+
+    Group k has sizes[k] particles: an NFW host truncated at its R_200 and
+    0..max_subs NFW subhaloes, each with a mass ratio uniform in sub_ratio
+    relative to the host, placed inside the host at sub_offset R_200
+    (isotropic), truncated at their own R_200.  Groups sit on non-overlapping
+    spheres separated by `margin` l_mean (more than b and l_FoF), so no pair
+    of particles of two groups is within reach of the kernel or the linking
+    length.  Returns (pos int32 [n, 3], ids uint64 [n], meta)."""
+    if BOX % side:
+        raise ValueError("side must divide 2^21")
+    u = BOX // side
+    rng = np.random.default_rng(seed)
+    G = sizes.size
+    nsub = rng.integers(0, max_subs + 1, G) if max_subs > 0 else np.zeros(G, np.int64)
+    comp_n, comp_c, comp_g, comp_off = [], [], [], []
+    ext = np.zeros(G)
+    for g in range(G):
+        ratios = rng.uniform(sub_ratio[0], sub_ratio[1], nsub[g]) if nsub[g] else np.zeros(0)
+        host = int(round(sizes[g] / (1.0 + ratios.sum())))
+        subs = [int(round(r * host)) for r in ratios]
+        subs = [s for s in subs if s >= min_sub]
+        host = int(sizes[g] - sum(subs))
+        rh = float(r200(host))
+        e = rh
+        comp_n.append(host); comp_c.append(rng.uniform(*c_range)); comp_g.append(g); comp_off.append(np.zeros(3))
+        for s in subs:
+            off = rng.uniform(*sub_offset) * rh * isotropic(rng, 1)[0]
+            comp_n.append(s); comp_c.append(rng.uniform(*c_range)); comp_g.append(g); comp_off.append(off)
+            e = max(e, float(np.linalg.norm(off)) + float(r200(s)))
+        ext[g] = e + 0.5 * margin
+    centres = _place_spheres(rng, ext, side)
+    comp_n = np.asarray(comp_n, np.int64)
+    comp_g = np.asarray(comp_g, np.int64)
+    cc = (centres[comp_g] + np.asarray(comp_off)) * u
+    pts = _halo_points(rng, cc, comp_n, np.asarray(comp_c), u)
+    n = int(comp_n.sum())
+    pos = np.mod(np.rint(pts).astype(np.int64), BOX).astype(np.int32)
+    ids = np.arange(n, dtype=np.uint64)
+    perm = rng.permutation(n)
+    meta = dict(side=side, u=u, n=n, groups=int(G), components=int(comp_n.size), largest=int(sizes.max()),
+                seed=seed)
+    return np.ascontiguousarray(pos[perm]), ids[perm], meta
+
+
+def batched(seed=SEED0 + 3, total=4_000_000, giant=2_000_000):
+    """About 4M particles as pre-formed groups of uneven size in a box of side
+    256 l_mean: sizes with equal particles per logarithmic interval on
+    [35, 2e6] and one forced group of 2e6, each group an NFW host plus 0-5
+    NFW subhaloes of mass ratio 0.01-0.3."""
+    rng = np.random.default_rng(seed)
+    sizes = group_sizes_particle_weighted(rng, 35, 2_000_000, total, giant=giant)
+    return preformed_groups(256, sizes, 5, (0.01, 0.3), seed=seed + 1)
+
+
+def batched_many(seed=SEED0 + 4, groups=100_000):
+    """100,000 small pre-formed groups (single NFW haloes of 35-45 particles,
+    about 4M particles) in a box of side 256 l_mean."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(35, 46, groups)
+    return preformed_groups(256, sizes, 0, (0.0, 0.0), seed=seed + 1)
