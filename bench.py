@@ -263,6 +263,146 @@ def slab_stream(cso, torch, local, flags, pos, ids, meta, n_slabs=64, mean_gap_s
     return out
 
 
+SERVED_SCALE = {
+    "served512": dict(box="served512", budget_gb=40, small=(), desc=(
+        "served stream: periodic box side 512 l_mean, 134,217,728 particles (40% background, 60% NFW haloes N in "
+        "[20, 2e6], 10% with satellites), delivered as 64 x-slabs of 8 l_mean (~2.1M particles) with Poisson "
+        "arrivals (mean gap 20 ms) under a 40 GB device budget")),
+    "served1024": dict(box="served1024", budget_gb=120, small=(64, 128, 256), desc=(
+        "served stream at scale: periodic box side 1024 l_mean, 1,073,741,824 particles (same mixture, N up to "
+        "1e7), delivered as 256 x-slabs of 1-4 columns of 2 l_mean with Poisson arrivals (mean gap 20 ms), "
+        "interleaved with independent boxes of side 64/128/256 (262k-16.8M particles), under a 120 GB budget")),
+}
+
+
+def served_at_scale(args, cso, torch, local, name):
+    """A box streamed as x-slabs through the served path (cso_submit /
+    cso_poll): slabs are generated untimed and kept in device memory, then
+    submitted in x order at their scheduled arrival times; latency =
+    completion - scheduled arrival.  Three passes over the same slabs: a
+    warm-up (workspaces grow), Poisson arrivals, and all slabs at once (the
+    throughput).  For the side-512 box the same particles also run as one
+    whole box (plain and batched schedules), and the stream's labels are
+    compared with the whole box's bit for bit."""
+    from paper_2110_11408_gb300 import synth
+    spec = SERVED_SCALE[name]
+    box = getattr(synth, spec["box"])()
+    workers = max(1, min(16, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    slabs = []
+    for k, pos, ids in box.slabs(workers=workers, shuffle_seed=box.seed + 99):
+        slabs.append((torch.from_numpy(pos).cuda(), torch.from_numpy(ids.view(np.int64)).cuda(),
+                      int(box.edges[k]), int(box.edges[k + 1])))
+    gen_s = time.perf_counter() - t0
+    small = []
+    for j, side in enumerate(spec["small"]):
+        pos, ids, meta = synth.medium_sample(side=side, seed=synth.SEED0 + 700 + j)
+        small.append((torch.from_numpy(pos).cuda(), torch.from_numpy(ids.view(np.int64)).cuda(), meta["u"]))
+    torch.cuda.synchronize()
+    n = sum(len(s[0]) for s in slabs)
+    params = cso.cso_params_default(box.u)
+    flags = cso.FLAG_BATCHED | cso.FLAG_SLOTS(4)
+    budget = spec["budget_gb"] << 30
+    rng = np.random.default_rng(box.seed + 7)
+
+    def one_pass(label, gaps, request_id):
+        ctx = cso.Context(local, budget_bytes=budget, flags=flags)
+        arrivals = np.cumsum(gaps) if gaps is not None else np.zeros(len(slabs))
+        n_small = 4 * len(small)
+        small_at = np.sort(rng.uniform(0, arrivals[-1] if gaps is not None else 0.0, n_small)) if small else []
+        bufs, tickets, sched, kinds = [], [], [], []
+        torch.cuda.synchronize()
+        t_base = cso.cso_clock() + 0.01
+        si = 0
+        for k, (pos, ids, x_lo, x_hi) in enumerate(slabs):
+            while si < len(small_at) and small_at[si] <= arrivals[k]:
+                sp, sd, su = small[si % len(small)]
+                target = t_base + small_at[si]
+                while cso.cso_clock() < target:
+                    pass
+                b = cso.Buffers(sp, sd, True, want=("l0", "l1", "l2"))
+                bufs.append(b)
+                sched.append(target)
+                kinds.append(-1)
+                tickets.append(ctx.submit(b, cso.cso_params_default(su)))
+                si += 1
+            target = t_base + arrivals[k]
+            while cso.cso_clock() < target:
+                pass
+            b = cso.Buffers(pos, ids, True, halo_cap=len(pos) // 20 + 64, x_lo=x_lo, x_hi=x_hi,
+                            request_id=request_id, want=("l0", "l1", "l2"))
+            bufs.append(b)
+            sched.append(target)
+            kinds.append(k)
+            tickets.append(ctx.submit(b, params))
+        for t in tickets:
+            done, rc = ctx.wait(t)
+            assert done and rc == 0, cso.cso_last_error()
+        done_t = np.array([cso.cso_ticket_times(ctx.h, t)[2] for t in tickets])
+        ctx.close()
+        lat = (done_t - np.array(sched)) * 1e3
+        kinds = np.array(kinds)
+        sl = kinds >= 0
+        away = kinds >= 1  # slab 0 waits for the periodic seam, which closes with the last slab
+        span = done_t[sl].max() - min(sched)
+        out = {"slabs": int(sl.sum()), "particles": n, "particles_per_s": n / span,
+               "p50_ms": float(np.percentile(lat[sl], 50)), "p99_ms": float(np.percentile(lat[sl], 99)),
+               "p50_ms_away_from_seam": float(np.percentile(lat[away], 50)),
+               "p99_ms_away_from_seam": float(np.percentile(lat[away], 99)),
+               "arrivals": ("Poisson, mean gap %.0f ms" % 20) if gaps is not None else "all at t = 0"}
+        if (~sl).any():
+            out["small_boxes"] = {"requests": int((~sl).sum()), "p50_ms": float(np.percentile(lat[~sl], 50)),
+                                  "p99_ms": float(np.percentile(lat[~sl], 99))}
+        return out, [b for b, kk in zip(bufs, kinds) if kk >= 0]
+
+    one_pass("warm-up", None, 9000)
+    poisson, _ = one_pass("poisson", rng.exponential(0.020, len(slabs)), 9001)
+    saturated, sbufs = one_pass("saturated", None, 9002)
+    whole = None
+    equal = None
+    if name == "served512":
+        dpos = torch.cat([s[0] for s in slabs])
+        dids = torch.cat([s[1] for s in slabs])
+        whole = {}
+        for sched_name, fl in (("batched", cso.FLAG_BATCHED), ("plain", 0)):
+            c = cso.Context(local, flags=fl)
+            b = cso.Buffers(dpos, dids, True, halo_cap=n // 20 + 64, want=("l0", "l1", "l2"))
+            cso.cso_find_groups(c.h, b, params)  # warm-up (workspace)
+            ms = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                st = torch.cuda.ExternalStream(cso.cso_stream(c.h))
+                e0.record(st)
+                cso.cso_find_groups(c.h, b, params)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            whole[sched_name] = {"ms": statistics.median(ms), "particles_per_s": n / (statistics.median(ms) / 1e3)}
+            if sched_name == "batched":
+                off, equal = 0, True
+                for sb in sbufs:
+                    m = sb.n
+                    for key in ("l0", "l1", "l2"):
+                        equal = equal and bool(torch.equal(sb.out[key], b.out[key][off:off + m]))
+                    off += m
+            c.close()
+            del b
+    peaks, _ = load_peaks()
+    line = {
+        "metric": "CompaSO particles/s (whole hot path: density, L0, L1, L2, catalogue)",
+        "value": saturated["particles_per_s"], "unit": "particles/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": n / saturated["particles_per_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": name, "desc": spec["desc"], "n_particles": n, "slabs": len(slabs),
+                   "budget_gb": spec["budget_gb"], "generation_s": gen_s, "seed": box.seed,
+                   "l2_flush": "working set > L2 (slabs of 2-8M particles, inputs %.1f GB)" % (n * 20 / 1e9)},
+        "e2e": None, "served": {"poisson": poisson, "saturated": saturated},
+        "whole_box": whole, "stream_equals_whole_box": equal,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def radial_stage(cso, local, flags, dpos, dids, params, steps):
     """Radial statistics (r_25/50/75/98 and V_max about the L2max com) of every
     L1 halo of the benchmark box: device time of the radial stage alone (an
@@ -362,7 +502,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS) + sorted(SERVED_SCALE))
     ap.add_argument("--plain", action="store_true", help="time the plain schedule as the headline (default: batched)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other schedule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -380,6 +520,8 @@ def main():
     from paper_2110_11408_gb300 import cso
 
     torch.cuda.set_device(local)
+    if args.workload in SERVED_SCALE:
+        return served_at_scale(args, cso, torch, local, args.workload)
     dist = None
     if ws > 1:
         import torch.distributed as dist

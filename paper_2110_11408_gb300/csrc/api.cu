@@ -224,6 +224,7 @@ int ctx_reserve(cso_ctx* c, long long n, long long ncell, bool host_io) {
   }
   c->ws.off = 0;
   c->ws.peak = 0;
+  c->ws.err = nullptr;  // each request points it at its own device word
   return CSO_OK;
 }
 

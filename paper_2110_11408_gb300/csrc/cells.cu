@@ -7,6 +7,9 @@
 // is handled per run by shifting the query point by one box length, never
 // per pair.  With side <= 2^14 grid units every |dx| inside the stencil is
 // below 2^15, so squared distances fit uint32 exactly.
+#include <limits.h>
+#include <math.h>
+
 #include "cells.cuh"
 
 namespace {
@@ -75,26 +78,38 @@ __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_
 
 // Sigma_s = sum over j != s with d < b2 of (b2 - d)   (Eq. 1 times b2).
 //
-// A warp takes 32 consecutive cell-sorted particles.  When all of them sit in
-// one cell (the common case wherever the work is: in dense cells) they share
-// the nine stencil rows, so the warp walks each row once: lanes 0-8 look the
-// rows up, every run is staged into shared memory 32 particles at a time (one
-// coalesced int4 load per lane, the next tile prefetched while the current
-// one is consumed) and each lane sums its own particle against the tile by
-// shared-memory broadcast.  Warps whose particles span several cells walk the
+// A warp takes 32 consecutive cell-sorted particles.  When they all sit in
+// one (y, z) row of cells and span at most max_span + 1 adjacent x cells
+// (the common case wherever the work is: in and around dense cells), they
+// share the nine stencil rows, each the union of their x ranges, which is one
+// contiguous run of the sorted array (plus a wrapped run at the periodic x
+// edge).  The warp walks each run once, 32 neighbours at a time: every lane
+// loads one neighbour of the next 32 (a coalesced int4 load, in flight while
+// the current 32 are summed) and stores it, shifted and with |c|^2, into the
+// warp's shared tile; each lane then sums its own particle against the tile
+// by shared-memory broadcast.  Warps whose particles span more cells walk the
 // stencil lane by lane.
 //
 // In the shared walk, offsets are taken from the warp's first particle o:
 // the query is q = p - o, a staged neighbour c = t - shift - o, and
-// d = |q|^2 + |c|^2 - 2 q.c.  The lane that stages c also stores |c|^2, so a
-// pair costs three multiply-adds, one add and one min.  The arithmetic is
-// modulo 2^32: every component of q - c is below 2 cells = 2^15 units, so the
-// true d is below 3 * 2^30 and the wrapped result is exact.
+// d = |q|^2 + |c|^2 - 2 q.c.  The staging lane stores |c|^2 beside c, so a
+// pair costs three multiply-adds, a min and an add:
+//   * in general, d is formed modulo 2^32 and min(d, b2) summed; it is exact
+//     because the true d of every staged pair is below 2^32 (max_span is
+//     chosen on the host so that ((max_span + 2)^2 + 8) cell^2 < 2^32);
+//   * when every true d is below 2^29 (cells below 4,730 grid units), the
+//     lane compares t = d - |q|^2 with its own bound b2 - |q|^2 as signed
+//     integers, which saves the add of |q|^2.
+// Sharing rows over up to three x cells instead of one cell cut the pass by
+// 3% on the 16.8M-particle box and 22% on the 2.1M-particle box (GB300); the
+// same walk with tiles staged by bulk copies (cp.async.bulk into
+// double-buffered shared tiles completing on an mbarrier) measured slower at
+// every tile size tried (64, 128, 256 particles), so the lanes load the tiles.
 //
-// Blocks run heaviest first: a cost pass estimates each block's pair count,
-// files the block under floor(log2(cost)) and the density launch takes block
-// order[blockIdx.x], so the dense-halo blocks start in the first wave instead
-// of forming the tail.
+// Blocks run heaviest first: a cost pass estimates each block's candidate
+// count, files the block under floor(log2(cost)) and the density launch takes
+// block order[blockIdx.x], so the dense-halo blocks start in the first wave
+// instead of forming the tail.
 constexpr int DENS_WARPS = 8;
 constexpr int DENS_CLASSES = 33;
 
@@ -103,15 +118,22 @@ __device__ __forceinline__ uint32_t sq3(int x, int y, int z) {
 }
 
 // min(d, b2) for the staged neighbour c = (offset, |offset|^2) and the query
-// with P = |q|^2 and a = -2 q
+// with P = |q|^2 and a = -2 q (modulo 2^32)
 __device__ __forceinline__ uint32_t dmin_dot(int4 c, uint32_t P, uint32_t ax, uint32_t ay, uint32_t az, uint32_t b2) {
   const uint32_t d = (uint32_t)c.w + P + ax * (uint32_t)c.x + ay * (uint32_t)c.y + az * (uint32_t)c.z;
   return d < b2 ? d : b2;
 }
 
+// min(d - P, b2 - P) as signed integers (every true d below 2^31)
+__device__ __forceinline__ int tmin_dot(int4 c, int ax, int ay, int az, int B) {
+  const int t = c.w + ax * c.x + ay * c.y + az * c.z;
+  return t < B ? t : B;
+}
+
 // The shared-walk setup of one warp: whether its valid particles share a
-// cell and, for lanes 0-8, the runs of stencil row (dz + 1) * 3 + (dy + 1):
-// main run [lo0, hi0) and the wrapped run [lo1, hi1) with its x shift sx1.
+// (y, z) cell row and a short x span, and, for lanes 0-8, the runs of stencil
+// row (dz + 1) * 3 + (dy + 1): main run [lo0, hi0) and the wrapped run
+// [lo1, hi1) with its x shift sx1.
 struct WarpRows {
   bool uniform;
   int src;  // first valid lane
@@ -119,32 +141,49 @@ struct WarpRows {
   int sy, sz, sx1;
 };
 
-__device__ __forceinline__ WarpRows warp_rows(const CellGrid& g, int4 p, bool valid, unsigned vmask, int lane) {
+__device__ __forceinline__ WarpRows warp_rows(const CellGrid& g, int4 p, bool valid, unsigned vmask, int lane,
+                                              int max_span) {
   WarpRows R{};
   const int nc = g.nc;
   const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc), tc = grid_col(g, p.x);
-  const long long cell = valid ? (long long)grid_cell(g, cz, cy, tc) : -1;
   R.src = __ffs(vmask) - 1;
-  const long long cell0 = __shfl_sync(0xffffffffu, cell, R.src);
-  R.uniform = __all_sync(0xffffffffu, !valid || cell == cell0);
+  const int yz = cz * nc + cy;
+  const int yz0 = __shfl_sync(0xffffffffu, yz, R.src);
+  const int tmin = __reduce_min_sync(0xffffffffu, valid ? tc : INT_MAX);
+  const int tmax = __reduce_max_sync(0xffffffffu, valid ? tc : INT_MIN);
+  R.uniform = __all_sync(0xffffffffu, !valid || yz == yz0) && tmax - tmin <= max_span;
   if (!R.uniform) return R;
-  const int ccy = __shfl_sync(0xffffffffu, cy, R.src), ccz = __shfl_sync(0xffffffffu, cz, R.src);
-  const XCells X = x_cells(g, __shfl_sync(0xffffffffu, tc, R.src));
+  int a = tmin, b = tmax, wl = -1, wr = -1;
+  if (!g.colmap) {
+    if (tmin > 0) a = tmin - 1; else wl = nc - 1;
+    if (tmax + 1 < nc) b = tmax + 1; else wr = 0;
+  } else {
+    // table columns tmin..tmax must be adjacent columns of the box
+    const int k = tmin + lane;
+    const bool gap = k < tmax && g.cols[k + 1] != (g.cols[k] + 1) % nc;
+    if (__any_sync(0xffffffffu, gap)) {
+      R.uniform = false;
+      return R;
+    }
+    if (tmin > 0 && g.cols[tmin - 1] == (g.cols[tmin] + nc - 1) % nc) a = tmin - 1;
+    if (tmax + 1 < g.ncols && g.cols[tmax + 1] == (g.cols[tmax] + 1) % nc) b = tmax + 1;
+  }
   if (lane < 9) {
+    const int ccy = yz0 % nc, ccz = yz0 / nc;
     const int zz = wrap_yz(ccz + lane / 3 - 1, nc, R.sz);
     const int yy = wrap_yz(ccy + lane % 3 - 1, nc, R.sy);
     const uint32_t* row = grid_row(g, zz, yy);
-    R.lo0 = row[X.a];
-    R.hi0 = row[X.b + 1];
-    if (X.wl >= 0) { R.lo1 = row[X.wl]; R.hi1 = row[X.wl + 1]; R.sx1 = CSO_BOX; }
-    if (X.wr >= 0) { R.lo1 = row[X.wr]; R.hi1 = row[X.wr + 1]; R.sx1 = -CSO_BOX; }
+    R.lo0 = row[a];
+    R.hi0 = row[b + 1];
+    if (wl >= 0) { R.lo1 = row[wl]; R.hi1 = row[wl + 1]; R.sx1 = CSO_BOX; }
+    if (wr >= 0) { R.lo1 = row[wr]; R.hi1 = row[wr + 1]; R.sx1 = -CSO_BOX; }
   }
   return R;
 }
 
 // cost class and in-class rank of every density block
 __global__ void __launch_bounds__(DENS_WARPS * 32) k_density_cost(CellGrid g, const int4* __restrict__ spos, int n,
-                                                                 const uint8_t* __restrict__ only,
+                                                                 const uint8_t* __restrict__ only, int max_span,
                                                                  uint8_t* __restrict__ cls,
                                                                  uint32_t* __restrict__ rank,
                                                                  uint32_t* __restrict__ counts) {
@@ -157,7 +196,7 @@ __global__ void __launch_bounds__(DENS_WARPS * 32) k_density_cost(CellGrid g, co
   const int4 p = s < n ? spos[s] : make_int4(0, 0, 0, 0);
   const unsigned vmask = __ballot_sync(0xffffffffu, valid);
   if (vmask) {
-    const WarpRows R = warp_rows(g, p, valid, vmask, lane);
+    const WarpRows R = warp_rows(g, p, valid, vmask, lane, max_span);
     unsigned long long c;
     if (R.uniform) {
       // candidates the shared walk streams
@@ -199,11 +238,18 @@ __global__ void k_density_order(const uint8_t* __restrict__ cls, const uint32_t*
   if (b < nb) order[first[cls[b]] + rank[b]] = (uint32_t)b;
 }
 
-__global__ void __launch_bounds__(DENS_WARPS * 32) k_density(CellGrid g, const int4* __restrict__ spos, int n,
-                                                            uint32_t b2, int include_self,
-                                                            long long* __restrict__ sigma,
-                                                            const uint8_t* __restrict__ only,
-                                                            const uint32_t* __restrict__ order) {
+// run r of the shared walk (r = 2 * row + wrapped): [lo, hi) and x shift
+__device__ __forceinline__ void run_bounds(const WarpRows& R, int r, uint32_t& lo, uint32_t& hi) {
+  lo = __shfl_sync(0xffffffffu, (r & 1) ? R.lo1 : R.lo0, r >> 1);
+  hi = __shfl_sync(0xffffffffu, (r & 1) ? R.hi1 : R.hi0, r >> 1);
+}
+
+template <bool SMALL>
+__global__ void __launch_bounds__(DENS_WARPS * 32, 4) k_density(CellGrid g, const int4* __restrict__ spos, int n,
+                                                                 uint32_t b2, int include_self,
+                                                                 long long* __restrict__ sigma,
+                                                                 const uint8_t* __restrict__ only,
+                                                                 const uint32_t* __restrict__ order, int max_span) {
   __shared__ int4 tile[DENS_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int blk = order ? (int)order[blockIdx.x] : (int)blockIdx.x;
@@ -212,49 +258,55 @@ __global__ void __launch_bounds__(DENS_WARPS * 32) k_density(CellGrid g, const i
   const int4 p = s < n ? spos[s] : make_int4(0, 0, 0, 0);
   const unsigned vmask = __ballot_sync(0xffffffffu, valid);
   if (!vmask) return;
-  const WarpRows R = warp_rows(g, p, valid, vmask, lane);
+  const WarpRows R = warp_rows(g, p, valid, vmask, lane, max_span);
   unsigned long long acc = 0;
   if (R.uniform) {
     const int ox = __shfl_sync(0xffffffffu, p.x, R.src), oy = __shfl_sync(0xffffffffu, p.y, R.src),
               oz = __shfl_sync(0xffffffffu, p.z, R.src);
     const int qx = p.x - ox, qy = p.y - oy, qz = p.z - oz;
     const uint32_t P = sq3(qx, qy, qz);
-    const uint32_t ax = (uint32_t)(-2 * qx), ay = (uint32_t)(-2 * qy), az = (uint32_t)(-2 * qz);
+    const int ax = -2 * qx, ay = -2 * qy, az = -2 * qz;
+    const int B = (int)(b2 - P);
+    int4* tl = tile[w];
+#pragma unroll 1
     for (int r = 0; r < 18; ++r) {
-      const int rr = r >> 1;
-      const uint32_t lo = __shfl_sync(0xffffffffu, (r & 1) ? R.lo1 : R.lo0, rr);
-      const uint32_t hi = __shfl_sync(0xffffffffu, (r & 1) ? R.hi1 : R.hi0, rr);
+      uint32_t lo, hi;
+      run_bounds(R, r, lo, hi);
       if (lo >= hi) continue;
       // the neighbour's image nearest the warp: t - shift
-      const int bx = ox + ((r & 1) ? __shfl_sync(0xffffffffu, R.sx1, rr) : 0);
-      const int by = oy + __shfl_sync(0xffffffffu, R.sy, rr), bz = oz + __shfl_sync(0xffffffffu, R.sz, rr);
+      const int bx = ox + ((r & 1) ? __shfl_sync(0xffffffffu, R.sx1, r >> 1) : 0);
+      const int by = oy + __shfl_sync(0xffffffffu, R.sy, r >> 1), bz = oz + __shfl_sync(0xffffffffu, R.sz, r >> 1);
       int4 next = lo + lane < hi ? spos[lo + lane] : make_int4(0, 0, 0, 0);
       for (uint32_t t0 = lo; t0 < hi; t0 += 32) {
         {
           const int cx = next.x - bx, cy = next.y - by, cz = next.z - bz;
-          tile[w][lane] = make_int4(cx, cy, cz, (int)sq3(cx, cy, cz));
+          tl[lane] = make_int4(cx, cy, cz, (int)sq3(cx, cy, cz));
         }
         __syncwarp();
         const uint32_t t1 = t0 + 32;
         if (t1 + lane < hi) next = spos[t1 + lane];
         const int m = hi - t0 < 32 ? (int)(hi - t0) : 32;
-        // sum of (b2 - min(d, b2)) over the tile = m b2 - sum of min(d, b2);
-        // terms are <= b2 <= 2^28: a uint32 partial holds up to 15 of them,
-        // flushed to 64 bits every 8
-        uint32_t part = 0;
-        unsigned long long mins = 0;
         int k = 0;
-        for (; k + 4 <= m; k += 4) {
-          part += dmin_dot(tile[w][k], P, ax, ay, az, b2) + dmin_dot(tile[w][k + 1], P, ax, ay, az, b2) +
-                  dmin_dot(tile[w][k + 2], P, ax, ay, az, b2) + dmin_dot(tile[w][k + 3], P, ax, ay, az, b2);
-          if (k & 4) {
+        if (SMALL) {
+          long long mins = 0;
+          for (; k + 4 <= m; k += 4) {
+            int part = tmin_dot(tl[k], ax, ay, az, B) + tmin_dot(tl[k + 1], ax, ay, az, B);
+            part += tmin_dot(tl[k + 2], ax, ay, az, B) + tmin_dot(tl[k + 3], ax, ay, az, B);
             mins += part;
-            part = 0;
           }
+          for (; k < m; ++k) mins += tmin_dot(tl[k], ax, ay, az, B);
+          acc += (unsigned long long)((long long)m * B - mins);
+        } else {
+          unsigned long long mins = 0;
+          const uint32_t uax = (uint32_t)ax, uay = (uint32_t)ay, uaz = (uint32_t)az;
+          for (; k + 4 <= m; k += 4) {
+            uint32_t part = dmin_dot(tl[k], P, uax, uay, uaz, b2) + dmin_dot(tl[k + 1], P, uax, uay, uaz, b2);
+            part += dmin_dot(tl[k + 2], P, uax, uay, uaz, b2) + dmin_dot(tl[k + 3], P, uax, uay, uaz, b2);
+            mins += part;
+          }
+          for (; k < m; ++k) mins += dmin_dot(tl[k], P, uax, uay, uaz, b2);
+          acc += (unsigned long long)m * b2 - mins;
         }
-        for (; k < m; ++k) part += dmin_dot(tile[w][k], P, ax, ay, az, b2);
-        mins += part;
-        acc += (unsigned long long)m * b2 - mins;
         __syncwarp();
       }
     }
@@ -262,7 +314,6 @@ __global__ void __launch_bounds__(DENS_WARPS * 32) k_density(CellGrid g, const i
     for_stencil(g, p.x, p.y, p.z, [&](uint32_t t, int xq, int yq, int zq) { acc += kern(spos[t], xq, yq, zq, b2); });
   }
   if (!valid) return;
-  // the particle met itself once at d = 0
   if (!include_self) acc -= b2;
   sigma[s] = (long long)acc;
 }
@@ -785,13 +836,22 @@ int cells_choose(long long b2, int* nc_out) {
   long long nc = (long long)floor((double)CSO_BOX / b);
   while (nc > 1 && (long double)CSO_BOX * CSO_BOX < (long double)b2 * nc * nc) --nc;
   while ((long double)CSO_BOX * CSO_BOX >= (long double)b2 * (nc + 1) * (nc + 1)) ++nc;
-  *nc_out = (int)nc;
   if (nc < 128) {
     cso_set_error("kernel radius b = %.0f grid units is too large (cells must be <= 2^14 units, u <= 40960)", b);
     return CSO_ERR_ARG;
   }
-  if (nc > 1290) {
-    cso_set_error("box too fine for one dense cell table (nc = %lld > 1290)", nc);
+  if (nc > CSO_MAX_NC) {
+    cso_set_error("kernel radius b = %.0f grid units is too small (more than %d cells per side)", b, CSO_MAX_NC);
+    return CSO_ERR_ARG;
+  }
+  *nc_out = (int)nc;
+  return CSO_OK;
+}
+
+int cells_check_dense(int nc) {
+  if (nc > CSO_MAX_DENSE_NC) {
+    cso_set_error("box too fine for one dense cell table (%d cells per side > %d): deliver it as x-slabs", nc,
+                  CSO_MAX_DENSE_NC);
     return CSO_ERR_ARG;
   }
   return CSO_OK;
@@ -823,6 +883,21 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
   return CSO_OK;
 }
 
+// Widest x span of a warp's shared walk for cells of nc per side, and whether
+// every staged squared distance stays below 2^29 (the signed form).  A staged
+// pair is at most (span + 2) cells apart in x and 2 cells in y and z.
+static void density_span(int nc, int* max_span, bool* small) {
+  const double side = ceil((double)CSO_BOX / nc);
+  int sp = 0;
+  for (int s = 2; s >= 0; --s)
+    if (((s + 2.0) * (s + 2.0) + 8.0) * side * side < 4294967296.0) {
+      sp = s;
+      break;
+    }
+  *max_span = sp;
+  *small = ((sp + 2.0) * (sp + 2.0) + 8.0) * side * side < 536870912.0;
+}
+
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,
                   unsigned long long* pairs, Workspace& ws, cudaStream_t st, const uint8_t* only) {
   if (n <= 0) return CSO_OK;
@@ -836,10 +911,16 @@ int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int i
     cso_set_error("workspace exhausted in the density pass");
     return CSO_ERR_BUDGET;
   }
+  int max_span;
+  bool small;
+  density_span(g.nc, &max_span, &small);
   CSO_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * DENS_CLASSES, st));
-  k_density_cost<<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, only, cls, rank, counts);
+  k_density_cost<<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, only, max_span, cls, rank, counts);
   k_density_order<<<CL(cdiv(nb, 256)), 256, 0, st>>>(cls, rank, counts, nb, order);
-  k_density<<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only, order);
+  if (small)
+    k_density<true><<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only, order, max_span);
+  else
+    k_density<false><<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only, order, max_span);
   if (pairs) k_count_pairs<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, pairs);
   CSO_CUDA(cudaGetLastError());
   ws.off = mark;

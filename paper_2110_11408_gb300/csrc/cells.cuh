@@ -110,7 +110,15 @@ __device__ __forceinline__ void for_stencil(const CellGrid& g, int x, int y, int
   }
 }
 
+// Cells per side for a kernel radius of sqrt(b2) grid units: the largest nc
+// with cells at least b wide, 128 <= nc <= CSO_MAX_NC.
+#define CSO_MAX_NC 16384
 int cells_choose(long long b2, int* nc_out);
+// A whole box keeps one dense table of nc^3 cells (uint32 cell keys, 16 GB at
+// most); finer boxes go through the slab stream, whose window tables cover only
+// the x columns holding resident particles.
+#define CSO_MAX_DENSE_NC 1290
+int cells_check_dense(int nc);
 // Counting sort of the particles into the cell table; inv (optional, n
 // entries) receives the sorted slot of every input particle.
 int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGrid& g, uint32_t* start,

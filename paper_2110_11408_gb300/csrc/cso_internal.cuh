@@ -51,6 +51,7 @@ struct Workspace {
   size_t peak = 0;
   size_t need = 0;  // bytes requested during a sizing pass
   bool sizing = false;
+  int* err = nullptr;  // device word set by a kernel whose bounded wait gave up (CSO_ERR_TIMEOUT)
   void* take(size_t bytes) {
     size_t o = (off + 255) & ~size_t(255);
     off = o + bytes;

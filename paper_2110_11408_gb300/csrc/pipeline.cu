@@ -402,6 +402,10 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
     cso_set_error("positions outside [0, 2^21)");
     return CSO_ERR_ARG;
   }
+  if (hm.timeout) {
+    cso_set_error("a bounded device wait gave up");
+    return CSO_ERR_TIMEOUT;
+  }
   c->stats[1] = nd;
   c->stats[2] = G;
 
@@ -663,6 +667,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   if (n == 0) return CSO_OK;
   int nc;
   CSO_TRY(cells_choose(p->b2, &nc));
+  CSO_TRY(cells_check_dense(nc));
   const long long ncell = (long long)nc * nc * nc;
   const bool host_in = !in->on_device, host_out = !out->on_device;
   CSO_TRY(ctx_reserve(c, n, ncell, host_in || host_out));
@@ -691,6 +696,7 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   }
   ALLOC(Meta, meta, 1);
   CSO_CUDA(cudaMemsetAsync(meta, 0, sizeof(Meta), st));
+  ws.err = &meta->timeout;
 
   // ---- bin ----
   S.mark("bin");
@@ -776,6 +782,10 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   c->stats[9] = (int64_t)ws.peak;
   c->stats[10] = g_cso_launches - launches0;
 #undef ALLOC
+  if (hm.timeout) {
+    cso_set_error("a bounded device wait gave up");
+    return CSO_ERR_TIMEOUT;
+  }
   if (nrows > out->halo_cap) {
     cso_set_error("catalogue has %d rows, halo_cap is %lld", nrows, (long long)out->halo_cap);
     return CSO_ERR_CAPACITY;

@@ -52,6 +52,8 @@ struct Meta {  // device counters read back by the host
   unsigned long long pairs, work1, work2;
   int bad;
   int tie_overflow;  // a run of equal (group, Sigma) keys too long for k_tie_fix
+  int timeout;       // a bounded device wait gave up (Workspace::err points here)
+  int pad_;
 };
 
 // dense particles taking part (all, or those of selected groups) and group roots

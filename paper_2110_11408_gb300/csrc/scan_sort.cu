@@ -1,4 +1,5 @@
-// Device-wide exclusive scan and stable LSD radix sort (8-bit digits).
+// Device-wide exclusive scan (single pass, decoupled look-back) and stable
+// LSD radix sort (8-bit digits).
 //
 // The radix sort ranks elements inside a tile with warp-level matching
 // (__match_any_sync): warp w owns a contiguous run of the tile and keeps a
@@ -8,10 +9,6 @@
 #include "cso_internal.cuh"
 
 namespace {
-
-constexpr int SCAN_THREADS = 256;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   int lane = threadIdx.x & 31;
@@ -42,65 +39,104 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem_w
   return total;
 }
 
-__global__ void k_tile_sums(const uint32_t* __restrict__ d, long long n, uint32_t* __restrict__ sums) {
-  __shared__ uint32_t sw[33];
-  long long base = (long long)blockIdx.x * SCAN_TILE;
-  uint32_t s = 0;
-#pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    long long i = base + (long long)k * SCAN_THREADS + threadIdx.x;
-    if (i < n) s += d[i];
-  }
-  uint32_t excl;
-  uint32_t tot = block_excl_scan(s, sw, excl);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+// Single-pass exclusive scan with decoupled look-back (Merrill and Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016).  Tiles
+// take their index from an atomic counter in the order they start, so every
+// predecessor of a tile is already running; each tile publishes its aggregate
+// (flag A), then warp 0 walks back over 32 predecessors at a time, adding
+// aggregates until it meets an inclusive prefix (flag P), and publishes its
+// own inclusive prefix.  A status word is flag << 32 | value.
+constexpr int SP_THREADS = 256;
+constexpr int SP_ITEMS = 16;
+constexpr int SP_TILE = SP_THREADS * SP_ITEMS;  // 4096 values per tile
+constexpr unsigned long long SP_A = 1ull << 32, SP_P = 2ull << 32;
+constexpr long long SP_SPIN_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ unsigned long long sp_load(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sp_store(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// single block: exclusive scan of m values (any m), total to *total
-__global__ void k_scan_single(uint32_t* __restrict__ d, long long m, uint32_t* total) {
+// status[0 .. ntiles) and the tile counter status[ntiles] start at zero
+__global__ void __launch_bounds__(SP_THREADS) k_scan_onepass(uint32_t* __restrict__ d, long long n,
+                                                             unsigned long long* __restrict__ status, long long ntiles,
+                                                             uint32_t* __restrict__ total, int* __restrict__ err) {
   __shared__ uint32_t sw[33];
-  uint32_t carry = 0;
-  for (long long base = 0; base < m; base += (long long)blockDim.x * SCAN_ITEMS) {
-    // each thread owns SCAN_ITEMS consecutive values
-    long long i0 = base + (long long)threadIdx.x * SCAN_ITEMS;
-    uint32_t v[SCAN_ITEMS];
-    uint32_t s = 0;
+  __shared__ long long tile_sh;
+  __shared__ uint32_t prefix_sh;
+  if (threadIdx.x == 0) tile_sh = (long long)atomicAdd(&status[ntiles], 1ull);
+  __syncthreads();
+  const long long tile = tile_sh;
+  const long long i0 = tile * SP_TILE + (long long)threadIdx.x * SP_ITEMS;
+  uint32_t v[SP_ITEMS];
+  if (i0 + SP_ITEMS <= n && ((reinterpret_cast<uintptr_t>(d + i0) & 15) == 0)) {
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-      v[k] = (i0 + k < m) ? d[i0 + k] : 0;
-      s += v[k];
+    for (int q = 0; q < SP_ITEMS / 4; ++q) {
+      const uint4 w = reinterpret_cast<const uint4*>(d + i0)[q];
+      v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
     }
-    uint32_t excl;
-    uint32_t tot = block_excl_scan(s, sw, excl);
-    uint32_t run = carry + excl;
+  } else {
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-      if (i0 + k < m) d[i0 + k] = run;
-      run += v[k];
-    }
-    carry += tot;
+    for (int k = 0; k < SP_ITEMS; ++k) v[k] = i0 + k < n ? d[i0 + k] : 0u;
   }
-  if (threadIdx.x == 0 && total) *total = carry;
-}
-
-__global__ void k_scan_tiles(uint32_t* __restrict__ d, long long n, const uint32_t* __restrict__ sums) {
-  __shared__ uint32_t sw[33];
-  long long base = (long long)blockIdx.x * SCAN_TILE;
-  long long i0 = base + (long long)threadIdx.x * SCAN_ITEMS;
-  uint32_t v[SCAN_ITEMS];
   uint32_t s = 0;
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    v[k] = (i0 + k < n) ? d[i0 + k] : 0;
-    s += v[k];
-  }
+  for (int k = 0; k < SP_ITEMS; ++k) s += v[k];
   uint32_t excl;
-  block_excl_scan(s, sw, excl);
-  uint32_t run = sums[blockIdx.x] + excl;
+  const uint32_t agg = block_excl_scan(s, sw, excl);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    uint32_t prefix = 0;
+    if (tile > 0) {
+      if (lane == 0) sp_store(&status[tile], SP_A | agg);
+      long long top = tile - 1;
+      long long spins = 0;
+      for (;;) {
+        const long long j = top - lane;
+        const unsigned long long w = j >= 0 ? sp_load(&status[j]) : SP_P;  // before tile 0: prefix 0
+        const unsigned long long flag = w & ~0xffffffffull;
+        const unsigned pmask = __ballot_sync(0xffffffffu, flag == SP_P);
+        const unsigned xmask = __ballot_sync(0xffffffffu, flag == 0);
+        const int firstP = pmask ? __ffs(pmask) - 1 : 31;
+        const unsigned need = firstP == 31 ? 0xffffffffu : ((2u << firstP) - 1u);
+        if (xmask & need) {  // a predecessor has not published yet
+          if (++spins > SP_SPIN_LIMIT) {
+            if (lane == 0) atomicExch(err, 1);
+            break;
+          }
+          continue;
+        }
+        prefix += __reduce_add_sync(0xffffffffu, lane <= firstP ? (uint32_t)w : 0u);
+        if (pmask) break;
+        top -= 32;
+      }
+    }
+    if (lane == 0) {
+      sp_store(&status[tile], SP_P | (uint32_t)(prefix + agg));
+      prefix_sh = prefix;
+      if (total && tile == ntiles - 1) *total = prefix + agg;
+    }
+  }
+  __syncthreads();
+  uint32_t run = prefix_sh + excl;
+  uint32_t o[SP_ITEMS];
 #pragma unroll
-  for (int k = 0; k < SCAN_ITEMS; ++k) {
-    if (i0 + k < n) d[i0 + k] = run;
+  for (int k = 0; k < SP_ITEMS; ++k) {
+    o[k] = run;
     run += v[k];
+  }
+  if (i0 + SP_ITEMS <= n && ((reinterpret_cast<uintptr_t>(d + i0) & 15) == 0)) {
+#pragma unroll
+    for (int q = 0; q < SP_ITEMS / 4; ++q)
+      reinterpret_cast<uint4*>(d + i0)[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < SP_ITEMS; ++k)
+      if (i0 + k < n) d[i0 + k] = o[k];
   }
 }
 
@@ -218,21 +254,19 @@ int scan_u32(uint32_t* data, long long n, uint32_t* total, Workspace& ws, cudaSt
     if (total) CSO_CUDA(cudaMemsetAsync(total, 0, sizeof(uint32_t), st));
     return CSO_OK;
   }
-  long long ntiles = cdiv(n, SCAN_TILE);
-  if (ntiles == 1) {
-    k_scan_single<<<CL(1), 1024, 0, st>>>(data, n, total);
-    CSO_CUDA(cudaGetLastError());
-    return CSO_OK;
+  if (!ws.err) {
+    cso_set_error("scan without a device error word");
+    return CSO_ERR_STATE;
   }
+  const long long ntiles = cdiv(n, SP_TILE);
   size_t mark = ws.off;
-  uint32_t* sums = ws.get<uint32_t>(ntiles);
-  if (!sums) {
+  unsigned long long* status = ws.get<unsigned long long>(ntiles + 1);
+  if (!status) {
     cso_set_error("workspace exhausted in scan");
     return CSO_ERR_BUDGET;
   }
-  k_tile_sums<<<CL((unsigned)ntiles), SCAN_THREADS, 0, st>>>(data, n, sums);
-  k_scan_single<<<CL(1), 1024, 0, st>>>(sums, ntiles, total);
-  k_scan_tiles<<<CL((unsigned)ntiles), SCAN_THREADS, 0, st>>>(data, n, sums);
+  CSO_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (ntiles + 1), st));
+  k_scan_onepass<<<CL((unsigned)ntiles), SP_THREADS, 0, st>>>(data, n, status, ntiles, total, ws.err);
   CSO_CUDA(cudaGetLastError());
   ws.off = mark;
   return CSO_OK;

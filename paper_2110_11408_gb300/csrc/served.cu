@@ -52,6 +52,8 @@ static size_t request_bytes(const cso_input* in, const cso_params* p, const cso_
     const long long cols = (long long)(in->x_hi - in->x_lo) * nc / CSO_BOX + 8;
     return workspace_bytes(3 * in->n + 4096, (cols < nc ? cols : nc) * nc * nc, false);
   }
+  *rc = cells_check_dense(nc);
+  if (*rc != CSO_OK) return 0;
   return workspace_bytes(in->n, (long long)nc * nc * nc, !in->on_device || !out->on_device) +
          (size_t)(in->n / 16 + 1024) * 2 * sizeof(cso_halo);
 }

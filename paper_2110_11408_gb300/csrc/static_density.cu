@@ -92,14 +92,15 @@ extern "C" int cso_density_static(const int32_t* pos, int64_t n, const cso_param
   int4* spos = ws.get<int4>(n);
   long long* ssig = ws.get<long long>(n);
   uint64_t* sid = ws.get<uint64_t>(n);
-  int* bad = ws.get<int>(1);
+  int* bad = ws.get<int>(2);  // [0] positions outside the box, [1] a bounded wait gave up
   if (!start || !spos || !ssig || !sid || !bad) {
     cso_set_error("cso_density_static: static scratch too small");
     return CSO_ERR_ARG;
   }
   // the array keeps the previous call's contents: counters start from zero
   // (cells_bin clears the cell table itself)
-  CSO_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+  CSO_CUDA(cudaMemsetAsync(bad, 0, 2 * sizeof(int), st));
+  ws.err = bad + 1;
   // ids play no part in densities: the binning pass copies n placeholder
   // words (the not yet written sums) into its id slot
   CellGrid g = whole_box_grid(nc, start);
@@ -107,12 +108,16 @@ extern "C" int cso_density_static(const int32_t* pos, int64_t n, const cso_param
   CSO_TRY(cells_density(g, spos, (int)n, (uint32_t)p.b2, p.include_self, ssig, nullptr, ws, st));
   k_unsort<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, ssig, (int)n, sigma);
   CSO_CUDA(cudaGetLastError());
-  int hbad = 0;
-  CSO_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int hbad[2] = {0, 0};
+  CSO_CUDA(cudaMemcpyAsync(hbad, bad, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CSO_CUDA(cudaStreamSynchronize(st));
-  if (hbad) {
+  if (hbad[0]) {
     cso_set_error("cso_density_static: positions outside [0, 2^21)");
     return CSO_ERR_ARG;
+  }
+  if (hbad[1]) {
+    cso_set_error("cso_density_static: a bounded device wait gave up");
+    return CSO_ERR_TIMEOUT;
   }
   return CSO_OK;
 }

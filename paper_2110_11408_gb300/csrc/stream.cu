@@ -340,6 +340,11 @@ int stream_step(cso_ctx* c, StreamState& S, const cso_input* in, cso_output* out
   }
   S.last_ncols = g.ncols;
   const long long ncell = (long long)g.ncols * nc * nc;
+  if (ncell + 1 >= (1ll << 32)) {
+    cso_set_error("slab window of %d columns of %d x %d cells exceeds 2^32 cells", g.ncols, nc, nc);
+    S.failed = true;
+    return CSO_ERR_BUDGET;
+  }
   CSO_TRY(ctx_reserve(c, NR, ncell, false));
   Workspace& ws = c->ws;
 #define ALLOC(T, name, cnt)                              \
@@ -406,6 +411,7 @@ int stream_step(cso_ctx* c, StreamState& S, const cso_input* in, cso_output* out
     ALLOC(Meta, meta, 1);
     // a window particle outside the window's columns sets meta->bad = 2
     CSO_CUDA(cudaMemsetAsync(meta, 0, sizeof(Meta), st));
+    ws.err = &meta->timeout;
     CSO_TRY(cells_bin(S.rpos[k], S.rid[k], NR, g, start, spos, sid, &meta->bad, ws, st));
 
     // ---- kernel sums of the columns that became final ----
@@ -462,9 +468,15 @@ int stream_step(cso_ctx* c, StreamState& S, const cso_input* in, cso_output* out
                                    S.ridx[k], S.rpos[o], S.rid[o], S.rsig[o], S.rflag[o], S.rslab[o], S.ridx[o]);
     CSO_CUDA(cudaGetLastError());
     CSO_CUDA(cudaMemcpyAsync(c->pinned, kscan + NR, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CSO_CUDA(cudaMemcpyAsync((char*)c->pinned + 8, &meta->timeout, sizeof(int), cudaMemcpyDeviceToHost, st));
     CSO_CUDA(cudaStreamSynchronize(st));
     S.nr = *(uint32_t*)c->pinned;
     S.cur = o;
+    if (*(int*)((char*)c->pinned + 8)) {
+      cso_set_error("a bounded device wait gave up");
+      S.failed = true;
+      return CSO_ERR_TIMEOUT;
+    }
   }
   S.col_fin = fin;
 

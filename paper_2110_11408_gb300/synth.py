@@ -334,3 +334,206 @@ def batched_many(seed=SEED0 + 4, groups=100_000):
     rng = np.random.default_rng(seed)
     sizes = rng.integers(35, 46, groups)
     return preformed_groups(256, sizes, 0, (0.0, 0.0), seed=seed + 1)
+
+
+# --------------------------------------------------------------------------
+# boxes delivered as x-slabs (the served workloads)
+# --------------------------------------------------------------------------
+
+def nfw_unit_radii_closed(q, c):
+    """Radii r / R_200 of NFW profiles of concentration c at enclosed-mass
+    fractions q * mu(c), by the closed-form inverse of mu(y) = ln(1 + y) -
+    y / (1 + y): with t = 1 / (1 + y), t - ln t = 1 + m, so
+    t = -W0(-exp(-1 - m)) (principal branch of Lambert's W)."""
+    from scipy.special import lambertw
+    c = np.asarray(c, np.float64)
+    m = np.asarray(q, np.float64) * _mu(c)
+    t = -lambertw(-np.exp(-1.0 - m), 0).real
+    return (1.0 / t - 1.0) / c
+
+
+class SlabBox:
+    """A periodic box of `side` l_mean of the NFW-halo recipe (uniform
+    background plus NFW haloes with optional satellites, as nfw_box), cut
+    into x-slabs at the grid coordinates `edges` (0 = edges[0] < ... <
+    edges[-1] = 2^21) and generated slab by slab with bounded memory.
+
+    The halo catalogue (sizes, concentrations, centres) is drawn first.  The
+    haloes whose centre lies in slab j form chunk j; a chunk's particles are
+    drawn from a generator seeded by (seed, j), so any chunk can be made in any
+    order (or in another process) and gives the same particles, which are
+    routed to the slabs they fall in.  Background particles of slab k come
+    from a generator seeded by (seed, k).  Ids: halo particles are numbered
+    chunk by chunk, then the background slab by slab.  NFW radii use the
+    closed-form inverse of the mass fraction."""
+
+    def __init__(self, side, frac_bg, nmin, nmax, edges, slope=-1.9, sat_frac=0.1, sat_ratio=(0.05, 0.3),
+                 sat_offset=(0.3, 1.5), c_range=(4.0, 12.0), seed=0):
+        if BOX % side:
+            raise ValueError("side must divide 2^21")
+        self.side, self.u, self.seed = side, BOX // side, seed
+        self.edges = np.asarray(edges, np.int64)
+        assert self.edges[0] == 0 and self.edges[-1] == BOX and np.all(np.diff(self.edges) > 0)
+        self.nslab = self.edges.size - 1
+        n = side ** 3
+        self.n = n
+        rng = np.random.default_rng(seed)
+        sizes, conc, parent, offset = _draw_haloes(rng, n - int(round(frac_bg * n)), nmin, nmax, slope, sat_frac,
+                                                   sat_ratio, sat_offset, c_range)
+        nh = sizes.size
+        centres = rng.random((nh, 3)) * side
+        sat = parent >= 0
+        if sat.any():
+            dirs = isotropic(rng, int(sat.sum()))
+            hp = parent[sat]
+            centres[sat] = centres[hp] + (offset[sat] * r200(sizes[hp]))[:, None] * dirs
+        centres = np.mod(centres, side)
+        self.sizes, self.conc, self.centres = sizes, conc, centres * self.u  # centres in grid units
+        self.n_halo = int(sizes.sum())
+        self.n_bg = n - self.n_halo
+        # chunks: haloes by the slab holding their centre
+        cx = self.centres[:, 0]
+        self.chunk_of = np.clip(np.searchsorted(self.edges, cx, side="right") - 1, 0, self.nslab - 1)
+        order = np.argsort(self.chunk_of, kind="stable")
+        self.halo_order = order
+        self.chunk_start = np.searchsorted(self.chunk_of[order], np.arange(self.nslab + 1))
+        pc = np.zeros(self.nslab + 1, np.int64)
+        np.add.at(pc, self.chunk_of + 1, sizes)
+        self.chunk_id0 = np.cumsum(pc)  # first id of each chunk
+        # the slabs a chunk can reach (haloes extend at most R_200 from their centre)
+        ext = r200(sizes) * self.u
+        self.chunk_reach = []
+        for j in range(self.nslab):
+            hs = order[self.chunk_start[j]:self.chunk_start[j + 1]]
+            if hs.size == 0:
+                self.chunk_reach.append(())
+                continue
+            lo = float((cx[hs] - ext[hs]).min()) - 2.0
+            hi = float((cx[hs] + ext[hs]).max()) + 2.0
+            self.chunk_reach.append(tuple(sorted(self._slabs_in(lo, hi))))
+        self.needs = [[] for _ in range(self.nslab)]
+        for j, ks in enumerate(self.chunk_reach):
+            for k in ks:
+                self.needs[k].append(j)
+        width = np.diff(self.edges).astype(np.float64)
+        bg = np.floor(self.n_bg * width / BOX).astype(np.int64)
+        bg[-1] += self.n_bg - int(bg.sum())
+        self.bg_count = bg
+        self.bg_id0 = self.n_halo + np.concatenate([[0], np.cumsum(bg)])
+
+    def _slabs_in(self, lo, hi):
+        """Slabs meeting the x interval [lo, hi) (grid units, may wrap)."""
+        out = set()
+        for a, b in ((lo, hi), (lo + BOX, hi + BOX), (lo - BOX, hi - BOX)):
+            a, b = max(a, 0.0), min(b, float(BOX))
+            if a >= b:
+                continue
+            k0 = int(np.searchsorted(self.edges, a, side="right") - 1)
+            k1 = int(np.searchsorted(self.edges, b, side="left"))
+            out.update(range(max(k0, 0), min(k1, self.nslab)))
+        return out
+
+    def chunk(self, j):
+        """Particles of the haloes of chunk j: {slab: (pos int32 [m, 3], ids uint64 [m])}."""
+        hs = self.halo_order[self.chunk_start[j]:self.chunk_start[j + 1]]
+        if hs.size == 0:
+            return {}
+        rng = np.random.default_rng([self.seed, 1, j])
+        sizes = self.sizes[hs]
+        k = np.repeat(np.arange(hs.size), sizes)
+        x = nfw_unit_radii_closed(rng.random(k.size), self.conc[hs][k])
+        rad = x * r200(sizes)[k] * self.u
+        pts = self.centres[hs][k] + rad[:, None] * isotropic(rng, k.size)
+        pos = np.mod(np.rint(pts).astype(np.int64), BOX).astype(np.int32)
+        ids = np.uint64(self.chunk_id0[j]) + np.arange(k.size, dtype=np.uint64)
+        dest = np.searchsorted(self.edges, pos[:, 0], side="right") - 1
+        out = {}
+        for s in np.unique(dest):
+            m = dest == s
+            out[int(s)] = (pos[m], ids[m])
+        return out
+
+    def background(self, k):
+        rng = np.random.default_rng([self.seed, 2, k])
+        m = int(self.bg_count[k])
+        x = rng.integers(self.edges[k], self.edges[k + 1], m)
+        yz = rng.integers(0, BOX, (m, 2))
+        pos = np.column_stack([x, yz]).astype(np.int32)
+        return pos, np.uint64(self.bg_id0[k]) + np.arange(m, dtype=np.uint64)
+
+    def slabs(self, workers=1, shuffle_seed=None):
+        """Yield (k, pos, ids) for k = 0 .. nslab - 1, in order.  workers > 1
+        draws chunks in a pool of spawned processes, a few slabs ahead."""
+        pending = {}  # slab -> list of (pos, ids)
+        done = set()
+        pool = None
+        futs = {}
+        if workers > 1:
+            import concurrent.futures as cf
+            import multiprocessing as mp
+            pool = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+
+        def submit(j):
+            if j in done or j in futs:
+                return
+            futs[j] = pool.submit(_slab_box_chunk, self, j) if pool else None
+
+        try:
+            for k in range(self.nslab):
+                if pool:
+                    for kk in range(k, min(k + 2 * workers, self.nslab)):
+                        for j in self.needs[kk]:
+                            submit(j)
+                for j in self.needs[k]:
+                    if j in done:
+                        continue
+                    parts = futs.pop(j).result() if (pool and j in futs) else self.chunk(j)
+                    futs.pop(j, None)
+                    done.add(j)
+                    for s, v in parts.items():
+                        pending.setdefault(s, []).append(v)
+                bp, bi = self.background(k)
+                got = pending.pop(k, [])
+                pos = np.concatenate([bp] + [p for p, _ in got])
+                ids = np.concatenate([bi] + [i for _, i in got])
+                if shuffle_seed is not None:
+                    perm = np.random.default_rng([shuffle_seed, k]).permutation(len(pos))
+                    pos, ids = pos[perm], ids[perm]
+                yield k, np.ascontiguousarray(pos), ids
+        finally:
+            if pool:
+                pool.shutdown(wait=True, cancel_futures=True)
+
+
+def _slab_box_chunk(box, j):
+    return box.chunk(j)
+
+
+def served512(seed=SEED0 + 5):
+    """Box 512 l_mean, 512^3 = 134M particles: 40% background, 60% in NFW
+    haloes of 20-2e6 particles (slope -1.9), 10% with satellites, delivered
+    as 64 x-slabs of 8 l_mean (~2.1M particles each)."""
+    edges = [BOX * k // 64 for k in range(65)]
+    return SlabBox(512, 0.4, 20, 2_000_000, edges, seed=seed)
+
+
+def served1024_edges(seed=SEED0 + 6):
+    """x-slab edges of the side-1024 stream: the 512 columns of 2 l_mean are
+    cut into 256 slabs of 1-4 columns by a seeded composition."""
+    rng = np.random.default_rng(seed)
+    parts = np.full(256, 2, np.int64)  # 512 columns; seeded moves of one column keep the sum and the range
+    src = rng.integers(0, 256, 8192)
+    dst = rng.integers(0, 256, 8192)
+    for i, j in zip(src, dst):
+        if i != j and parts[i] > 1 and parts[j] < 4:
+            parts[i] -= 1
+            parts[j] += 1
+    cols = np.concatenate([[0], np.cumsum(parts)])
+    return [int(c) * (BOX // 512) for c in cols]
+
+
+def served1024(seed=SEED0 + 7):
+    """Box 1024 l_mean, 1024^3 = 1.07e9 particles (12.9 GB of positions): the
+    same mixture with haloes up to 1e7 particles, delivered as 256 x-slabs of
+    1-4 columns of 2 l_mean."""
+    return SlabBox(1024, 0.4, 20, 10_000_000, served1024_edges(), seed=seed)
