@@ -356,7 +356,7 @@ def served_at_scale(args, cso, torch, local, name):
         return out, [b for b, kk in zip(bufs, kinds) if kk >= 0]
 
     one_pass("warm-up", None, 9000)
-    poisson, _ = one_pass("poisson", rng.exponential(0.020, len(slabs)), 9001)
+    poisson = one_pass("poisson", rng.exponential(0.020, len(slabs)), 9001)[0]
     saturated, sbufs = one_pass("saturated", None, 9002)
     whole = None
     equal = None
@@ -644,6 +644,24 @@ def main():
         d2h = n * 8 * 4 + int(hb.cout.n_halos) * cso.HALO_DTYPE.itemsize
         e2e = {"value": ws * n / dt, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # the paper's radial-bin threshold-radius search against the default
+    # threshold-count binning: device time of the CompaSO level stages
+    r_search = None
+    if not args.no_compare and ws == 1:
+        r_search = {}
+        for label, fl in (("threshold_count_bins", 0), ("radial_bins", cso.FLAG_RADIAL_BINS)):
+            c3 = cso.Context(local, flags=flags | fl)
+            if tuned:
+                cso.cso_set_schedule(c3.h, tuned[0], tuned[1])
+            lv = []
+            for rep in range(args.warmup + args.steps):
+                cso.cso_find_groups(c3.h, buf, params)
+                st3 = cso.cso_stage_times(c3.h)
+                if rep >= args.warmup:
+                    lv.append(st3.get("level1", 0.0) + st3.get("level2", 0.0))
+            c3.close()
+            r_search[label + "_levels_ms"] = statistics.median(lv)
+
     radial = None
     if not args.no_radial and ws == 1:
         radial = radial_stage(cso, local, flags & ~cso.FLAG_TIMING, dpos, dids, params, args.steps)
@@ -687,7 +705,7 @@ def main():
                    % (n * 20 / 1e6, cell_table_bytes(meta["u"]) / 1e9), "seed": meta["seed"]},
         "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all, "clocks": clocks, "served": served, "other_schedule": other,
-        "radial": radial,
+        "radial": radial, "r_search": r_search,
         "stages_ms": stages,
         "counts": {k: stats[k] for k in ("dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows",
                                          "pairs_b", "l1_work", "l2_work", "workspace_bytes")},

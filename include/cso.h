@@ -52,6 +52,11 @@ extern "C" {
  * sizes are read back from the device between stages) */
 #define CSO_FLAG_COUNT_PAIRS 8u /* count kernel pairs with d < b2 (cso_last_stats[6]); slows the density pass */
 #define CSO_FLAG_SELECT_STRESS 16u /* testing: tiny radius-search tiles so every select branch runs; same results */
+/* threshold-radius search by the paper's radial bins (Sec. 2.3.4): members
+ * are binned outward in steps of sqrt(3)/3 cell sides and a bin is skipped
+ * while the members inside it, placed at its outer edge, still meet the
+ * threshold; the default bins by threshold count.  Same R^2 either way. */
+#define CSO_FLAG_RADIAL_BINS 32u
 /* served path: number of worker slots (concurrent requests), 1..15; 0 = 4 */
 #define CSO_FLAG_SLOTS(k) ((uint32_t)((k) & 0xf) << 8)
 
@@ -245,6 +250,37 @@ int cso_autotune(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_out
 /* Set the batched schedule's size bins directly (giant >= 64, 1 <= small
  * <= 64); the defaults are 16384 and 64. */
 int cso_set_schedule(cso_ctx* ctx, int32_t giant, int32_t small);
+
+/* --- the three steps one at a time --------------------------------------
+ *
+ * For a caller that distributes one box over several GPUs (each GPU owns
+ * x-slabs, the strict slab segmentation of Sec. 2.1) and exchanges ghost
+ * particles and cross-boundary groups between the steps.  Each call is
+ * synchronous on the context's stream and bins its particles like
+ * cso_find_groups; chained on one box they give cso_find_groups' outputs.
+ * pos int32[n][3], ids uint64[n] and the per-particle arrays are in input
+ * order, host or device memory as on_device (out->on_device for cso_levels)
+ * says; the caller owns every buffer.  Errors as cso_find_groups. */
+
+/* Kernel sums Sigma_i = sum_{j != i, d_ij < b2} (b2 - d_ij) (Sec. 2.2.1,
+ * Eq. 1 times b2) of the first n_query particles, every one of the n
+ * particles counting as a neighbour (the rest are the caller's ghosts). */
+int cso_density(cso_ctx* ctx, const int32_t* pos, int64_t n, int64_t n_query, const cso_params* p, int64_t* sigma,
+                int32_t on_device);
+
+/* L0 groups (Sec. 2.2.1) of n particles whose kernel sums the caller gives:
+ * particles with Sigma > T_L0 link when d < lfof2; l0[i] = smallest id of
+ * i's group, CSO_NO_GROUP for the others. */
+int cso_fof(cso_ctx* ctx, const int32_t* pos, const uint64_t* ids, const int64_t* sigma, int64_t n,
+            const cso_params* p, uint64_t* l0, int32_t on_device);
+
+/* L1 and L2 (Sec. 2.2.2) inside the groups the caller's labels l0 define
+ * (equal labels = one group, CSO_NO_GROUP = in none), with the kernel sums
+ * sigma: out->l1, out->l2 (either may be NULL) and the catalogue as
+ * cso_find_groups writes them; out->l0, out->sigma and out->radial are not
+ * used (radial must be NULL). */
+int cso_levels(cso_ctx* ctx, const int32_t* pos, const uint64_t* ids, const int64_t* sigma, const uint64_t* l0,
+               int64_t n, const cso_params* p, cso_output* out);
 
 /* --- introspection ------------------------------------------------------ */
 

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcso.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "pipeline.cu", "cells.cu", "compaso.cu", "scan_sort.cu", "static_density.cu", "served.cu", "stream.cu", "radial.cu", "probe.cu"]
+SOURCES = ["api.cu", "pipeline.cu", "cells.cu", "compaso.cu", "scan_sort.cu", "static_density.cu", "served.cu", "stream.cu", "radial.cu", "probe.cu", "stages.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -33,6 +33,7 @@ CSO_STATIC_MAX_N = 1 << 20
 CSO_STATIC_MAX_CELLS = 1 << 22
 
 FLAG_BATCHED = 1
+FLAG_RADIAL_BINS = 32
 FLAG_TIMING = 2
 FLAG_COUNT_PAIRS = 8
 FLAG_SELECT_STRESS = 16
@@ -143,6 +144,12 @@ def lib(build_if_missing=True):
         L.cso_clock.restype = ctypes.c_double
         L.cso_struct_sizes.argtypes = [P(ctypes.c_int64), ctypes.c_int]
         L.cso_probe_peaks.argtypes = [ctypes.c_int, P(ctypes.c_double), ctypes.c_int]
+        L.cso_density.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, P(CsoParams),
+                                  ctypes.c_void_p, ctypes.c_int32]
+        L.cso_fof.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                              P(CsoParams), ctypes.c_void_p, ctypes.c_int32]
+        L.cso_levels.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_int64, P(CsoParams), P(CsoOutput)]
         _lib = L
     return _lib
 
@@ -262,6 +269,47 @@ def cso_find_groups(ctx, buffers, params):
     rc = lib().cso_find_groups(ctx, ctypes.byref(buffers.cin), ctypes.byref(params), ctypes.byref(buffers.cout))
     _check(rc, "cso_find_groups")
     return rc
+
+
+def cso_density(ctx, pos, n_query, params):
+    """Kernel sums of the first n_query particles of pos (numpy int32 [n, 3]),
+    every particle a neighbour; numpy int64 [n_query]."""
+    pos = np.ascontiguousarray(pos, np.int32)
+    out = np.empty(int(n_query), np.int64)
+    _check(lib().cso_density(ctx, _ptr(pos), pos.shape[0], int(n_query), ctypes.byref(params), _ptr(out), 0),
+           "cso_density")
+    return out
+
+
+def cso_fof(ctx, pos, ids, sigma, params):
+    """L0 labels (smallest id of the group, NO_GROUP if not dense) of the given
+    particles with the given kernel sums; numpy uint64 [n]."""
+    pos = np.ascontiguousarray(pos, np.int32)
+    ids = np.ascontiguousarray(ids).view(np.uint64)
+    sigma = np.ascontiguousarray(sigma, np.int64)
+    out = np.empty(pos.shape[0], np.uint64)
+    _check(lib().cso_fof(ctx, _ptr(pos), _ptr(ids), _ptr(sigma), pos.shape[0], ctypes.byref(params), _ptr(out), 0),
+           "cso_fof")
+    return out
+
+
+def cso_levels(ctx, pos, ids, sigma, l0, params, halo_cap=None):
+    """L1 and L2 labels and the catalogue inside the groups that the labels
+    l0 define; returns (l1, l2, halos) as numpy arrays."""
+    pos = np.ascontiguousarray(pos, np.int32)
+    ids = np.ascontiguousarray(ids).view(np.uint64)
+    sigma = np.ascontiguousarray(sigma, np.int64)
+    l0 = np.ascontiguousarray(l0).view(np.uint64)
+    n = pos.shape[0]
+    cap = int(halo_cap if halo_cap is not None else max(16, n // 35 + 1))
+    l1 = np.empty(n, np.uint64)
+    l2 = np.empty(n, np.uint64)
+    halos = np.empty(cap, HALO_DTYPE)
+    out = CsoOutput(l0=None, l1=_ptr(l1), l2=_ptr(l2), sigma=None, halos=_ptr(halos), halo_cap=cap, n_halos=0,
+                    on_device=0, radial=None)
+    _check(lib().cso_levels(ctx, _ptr(pos), _ptr(ids), _ptr(sigma), _ptr(l0), n, ctypes.byref(params),
+                            ctypes.byref(out)), "cso_levels")
+    return l1, l2, halos[:out.n_halos].copy()
 
 
 def cso_autotune(ctx, buffers, params):

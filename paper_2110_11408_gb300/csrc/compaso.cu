@@ -197,6 +197,20 @@ __device__ __forceinline__ int pow2_at_least(int m) {
   return p;
 }
 
+// Bin of distance d in the first window of the select.  Both binnings are
+// monotone in d, and the select only prunes with the exact predicate at each
+// bin's largest member distance, so both give the same R^2:
+//   * threshold-count bins (default): bin = sqrt(K) d^1.5 / u^3 / w with
+//     w = n / (nb - 1) members of threshold count per bin;
+//   * radial bins (the paper's cell-bounded search, Sec. 2.3.4): bins of
+//     width sqrt(3)/3 cell sides in r; a bin is skipped when the members
+//     inside it, placed at its outer edge, still meet the threshold.
+__device__ __forceinline__ int first_bin(unsigned long long d, const PredConst& c, float scale0, int nb) {
+  const float f = (float)d;
+  const float g = c.radial ? sqrtf(f) * c.rbin_inv_w : f * sqrtf(f) * scale0;
+  return g < (float)(nb - 1) ? (int)g : nb - 1;
+}
+
 // R^2 of nucleus pc over the n members at epos[0..n); distances left in ed.
 template <int NT>
 __device__ long long r_search(const int4* __restrict__ epos, long long* __restrict__ ed, int n, int4 pc,
@@ -288,9 +302,7 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
       if (d < wlo || d > whi) continue;
       int b;
       if (mode == 0) {
-        float f = (float)d;
-        float g = f * sqrtf(f) * scale0;
-        b = g < (float)(nb - 1) ? (int)g : nb - 1;
+        b = first_bin(d, c, scale0, nb);
       } else {
         b = (int)(((d - wlo) * (unsigned long long)nb) / span);
       }
@@ -718,9 +730,7 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
         if (d < wlo || d > whi) continue;
         int b;
         if (mode == 0) {
-          const float f = (float)d;
-          const float g = f * sqrtf(f) * scale0;
-          b = g < (float)(nb - 1) ? (int)g : nb - 1;
+          b = first_bin(d, c, scale0, nb);
         } else {
           b = (int)(((d - wlo) * (unsigned long long)nb) / span);
         }
@@ -1177,5 +1187,7 @@ PredConst make_pred_const(double K, long long u) {
   c.u6 = ud * ud * ud * ud * ud * ud;
   // bin of the first window: threshold count sqrt(K) d^1.5 / u^3 (before /w)
   c.bin_scale0 = (float)(sqrt(K) / (ud * ud * ud));
+  c.radial = 0;
+  c.rbin_inv_w = 0.0f;
   return c;
 }

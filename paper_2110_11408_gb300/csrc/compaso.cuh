@@ -10,6 +10,8 @@ struct PredConst {
   int Ke;
   unsigned long long u;
   float bin_scale0;         // sqrt(K) / u^3
+  int radial;               // first window in radial bins of width sqrt(3)/3 cell sides (Sec. 2.3.4)
+  float rbin_inv_w;         // 1 / that width, per grid unit
 };
 PredConst make_pred_const(double K, long long u);
 

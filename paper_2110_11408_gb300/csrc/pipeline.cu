@@ -13,6 +13,7 @@
 //   halos    per-halo statistics and the catalogue (optionally the radial
 //            statistics and the shrinking-sphere centre)
 //   output   labels and kernel sums in input order
+#include <math.h>
 #include <string.h>
 
 #include "cells.cuh"
@@ -475,6 +476,11 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   L1.egs = gs;
   L1.T_min = p->T_min_L1;
   L1.pc = make_pred_const(p->K_L1, (long long)p->l_mean_grid);
+  const bool radial_bins = (c->flags & CSO_FLAG_RADIAL_BINS) != 0;
+  // radial bins of sqrt(3)/3 cell sides (cells of 2^21 / nc grid units)
+  const float rbin_inv_w = (float)(sqrt(3.0) * g.nc / (double)CSO_BOX);
+  L1.pc.radial = radial_bins;
+  L1.pc.rbin_inv_w = rbin_inv_w;
   L1.alpha_num = p->alpha_num;
   L1.alpha_den = p->alpha_den;
   L1.roche_num = p->roche_num;
@@ -561,6 +567,8 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   L2.slab = lab1;
   L2.T_min = p->T_min_L2;
   L2.pc = make_pred_const(p->K_L2, (long long)p->l_mean_grid);
+  L2.pc.radial = radial_bins;
+  L2.pc.rbin_inv_w = rbin_inv_w;
   L2.eslot = eslot2;
   L2.nuc_member = nucm2;
   L2.nuc_R2 = nucR22;
