@@ -41,10 +41,10 @@ WORKLOADS = {
                               "in a side-256 box"),
 }
 OPS_PER_PAIR = 11  # 3 sub, 3 mul, 2 add for d; compare; b2 - d; accumulate
-# DRAM bytes (read + write) of one k_density launch on the medium box, from
-# the single-pass ncu capture summarised in profiles/density_medium_dram.md;
-# valid for that kernel as it stands, and only for the medium workload
-DENSITY_DRAM_BYTES = {"medium": 3.25e9 + 135.21e6}
+# DRAM bytes (read + write) of one k_density launch per workload, from the
+# single-pass ncu capture summarised in profiles/ (only for the kernel as it
+# stands; absent workloads report null)
+DENSITY_DRAM_BYTES = {"medium": 3.2497e9}
 
 
 def cell_table_bytes(u):
@@ -275,7 +275,7 @@ SERVED_SCALE = {
 }
 
 
-def served_at_scale(args, cso, torch, local, name):
+def served_at_scale(args, cso, torch, local, name, emit=True):
     """A box streamed as x-slabs through the served path (cso_submit /
     cso_poll): slabs are generated untimed and kept in device memory, then
     submitted in x order at their scheduled arrival times; latency =
@@ -400,7 +400,9 @@ def served_at_scale(args, cso, torch, local, name):
         "e2e": None, "served": {"poisson": poisson, "saturated": saturated},
         "whole_box": whole, "stream_equals_whole_box": equal,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def radial_stage(cso, local, flags, dpos, dids, params, steps):
@@ -644,6 +646,29 @@ def main():
         d2h = n * 8 * 4 + int(hb.cout.n_halos) * cso.HALO_DTYPE.itemsize
         e2e = {"value": ws * n / dt, "unit": "particles/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # the batched step with its CompaSO level stages replayed as captured
+    # CUDA graphs, against direct launches
+    graph = None
+    if not args.no_compare and ws == 1 and not args.plain:
+        def step_ms(fl):
+            c4 = cso.Context(local, flags=fl)
+            if tuned:
+                cso.cso_set_schedule(c4.h, tuned[0], tuned[1])
+            s4 = torch.cuda.ExternalStream(cso.cso_stream(c4.h))
+            for _ in range(args.warmup):
+                cso.cso_find_groups(c4.h, buf, params)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s4)
+            for _ in range(args.steps):
+                cso.cso_find_groups(c4.h, buf, params)
+            e1.record(s4)
+            torch.cuda.synchronize()
+            c4.close()
+            return e0.elapsed_time(e1) / args.steps
+        base_fl = cso.FLAG_BATCHED
+        graph = {"ms_per_step_direct": step_ms(base_fl), "ms_per_step_graph": step_ms(base_fl | cso.FLAG_GRAPH)}
+
     # the paper's radial-bin threshold-radius search against the default
     # threshold-count binning: device time of the CompaSO level stages
     r_search = None
@@ -670,6 +695,13 @@ def main():
     if not args.no_served and ws == 1:
         served = {"boxes": served_stream(cso, torch, local, flags & ~cso.FLAG_TIMING),
                   "slab_stream": slab_stream(cso, torch, local, flags & ~cso.FLAG_TIMING, pos, ids, meta)}
+        if args.workload == "medium":
+            # the served configuration of side 512 (134M particles in 64 slabs)
+            s5 = served_at_scale(args, cso, torch, local, "served512", emit=False)
+            served["served512"] = {"desc": s5["config"]["desc"], "n_particles": s5["config"]["n_particles"],
+                                   "stream": s5["served"], "whole_box": s5["whole_box"],
+                                   "stream_equals_whole_box": s5["stream_equals_whole_box"]}
+            torch.cuda.empty_cache()
 
     if rank != 0:
         if dist is not None:
@@ -705,7 +737,7 @@ def main():
                    % (n * 20 / 1e6, cell_table_bytes(meta["u"]) / 1e9), "seed": meta["seed"]},
         "e2e": e2e, "gpu_launches": stats_t["launches"] * args.steps, "roofline": roof, "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all, "clocks": clocks, "served": served, "other_schedule": other,
-        "radial": radial, "r_search": r_search,
+        "radial": radial, "r_search": r_search, "level_graph": graph,
         "stages_ms": stages,
         "counts": {k: stats[k] for k in ("dense", "l0_groups", "l1_nuclei", "l2_nuclei", "catalogue_rows",
                                          "pairs_b", "l1_work", "l2_work", "workspace_bytes")},

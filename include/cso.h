@@ -48,8 +48,12 @@ extern "C" {
 #define CSO_FLAG_BATCHED 1u /* CompaSO levels by group size: warp, 256- and 1024-thread blocks, 8-CTA clusters,
                               largest first, on three concurrent streams */
 #define CSO_FLAG_TIMING 2u  /* record per-stage CUDA events (cso_stage_times) */
-/* value 4 is unused: the step is not captured as a CUDA graph (its launch
- * sizes are read back from the device between stages) */
+/* with CSO_FLAG_BATCHED: each CompaSO level stage (size sort, work queue and
+ * the four persistent tier kernels) is captured once as a CUDA graph and
+ * replayed by later calls with identical launch arguments (a box of the same
+ * shape in the same context); the rest of the step is launched directly (its
+ * launch sizes are read back from the device between stages) */
+#define CSO_FLAG_GRAPH 4u
 #define CSO_FLAG_COUNT_PAIRS 8u /* count kernel pairs with d < b2 (cso_last_stats[6]); slows the density pass */
 #define CSO_FLAG_SELECT_STRESS 16u /* testing: tiny radius-search tiles so every select branch runs; same results */
 /* threshold-radius search by the paper's radial bins (Sec. 2.3.4): members

@@ -33,6 +33,7 @@ CSO_STATIC_MAX_N = 1 << 20
 CSO_STATIC_MAX_CELLS = 1 << 22
 
 FLAG_BATCHED = 1
+FLAG_GRAPH = 4
 FLAG_RADIAL_BINS = 32
 FLAG_TIMING = 2
 FLAG_COUNT_PAIRS = 8

@@ -169,6 +169,8 @@ extern "C" void cso_free(cso_ctx* c) {
   if (c->pinned) cudaFreeHost(c->pinned);
   for (int i = 0; i <= CSO_MAX_STAGES; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (int i = 0; i < CSO_LEVEL_GRAPHS; ++i)
+    if (c->graphs[i].exec) cudaGraphExecDestroy(c->graphs[i].exec);
   if (c->side) cudaStreamSynchronize(c->side);
   if (c->side2) cudaStreamSynchronize(c->side2);
   if (c->join2) cudaEventDestroy(c->join2);

@@ -13,6 +13,7 @@
 //   pass B  tentative membership / competitive reassignment (Eq. 3) and
 //           eligibility marking.
 #include <cooperative_groups.h>
+#include <atomic>
 #include <float.h>
 #include <limits.h>
 
@@ -835,15 +836,10 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
   return R2;
 }
 
-__global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
-    k_level_cluster(LevelArgs a, const uint32_t* __restrict__ segs) {
-  __shared__ SelShared S;
-  __shared__ ClusterCtl C;
-  __shared__ ClusterGen G;
+__device__ void cluster_level(const LevelArgs& a, const int seg, SelShared& S, ClusterCtl& C, ClusterGen& G) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const bool leader = rank == 0;
-  const int seg = (int)segs[blockIdx.x / CL_CS];
   const unsigned base = a.seg_off[seg];
   const int n = (int)(a.seg_off[seg + 1] - base);
   const int tid = threadIdx.x;
@@ -952,6 +948,68 @@ __global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
   // no CTA may exit while another can still read its shared memory (the last
   // read of the leader's C.e happens after the final barrier of the loop)
   cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// The batched schedule's work queue: the groups sorted by size (largest
+// first) and cut into four size bins on the device -- giants, large, medium
+// and small -- with one fetch counter per bin.  Four persistent kernels pull
+// from it concurrently: 8-CTA clusters take giants, 1024-thread blocks large
+// groups, 256-thread blocks medium ones and warps the small ones, each taking
+// the next group of its bin when it finishes one, so no launch size depends
+// on a count read back by the host.
+// ---------------------------------------------------------------------------
+struct TierQueue {
+  unsigned count[4];  // giant, large, small (from k_seg_sizes); [3] unused
+  unsigned next[4];   // fetch counters: giant, large, medium, small
+  unsigned nseg;
+};
+
+// first index in the size-sorted order and count of bin t
+__device__ __forceinline__ void tier_range(const TierQueue& q, int t, unsigned& first, unsigned& cnt) {
+  const unsigned ng = q.count[0], nl = q.count[1], ns = q.count[2];
+  const unsigned nm = q.nseg - ng - nl - ns;
+  if (t == 0) { first = 0; cnt = ng; }
+  else if (t == 1) { first = ng; cnt = nl; }
+  else if (t == 2) { first = ng + nl; cnt = nm; }
+  else { first = q.nseg - ns; cnt = ns; }
+}
+
+__global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
+    k_level_cluster_q(LevelArgs a, const uint32_t* __restrict__ order, TierQueue* q) {
+  __shared__ SelShared S;
+  __shared__ ClusterCtl C;
+  __shared__ ClusterGen G;
+  __shared__ unsigned item;
+  cg::cluster_group cluster = cg::this_cluster();
+  const bool leader = cluster.block_rank() == 0;
+  unsigned first, cnt;
+  tier_range(*q, 0, first, cnt);
+  for (;;) {
+    if (leader && threadIdx.x == 0) item = atomicAdd(&q->next[0], 1u);
+    cluster.sync();
+    const unsigned it = *cluster.map_shared_rank(&item, 0);
+    cluster.sync();  // every CTA has read the leader's item before it changes
+    if (it >= cnt) return;
+    cluster_level(a, (int)order[first + it], S, C, G);
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_level_q(LevelArgs a, const uint32_t* __restrict__ order, TierQueue* q,
+                                                int tier) {
+  __shared__ unsigned item;
+  unsigned first, cnt;
+  tier_range(*q, tier, first, cnt);
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(&q->next[tier], 1u);
+    __syncthreads();
+    const unsigned it = item;
+    __syncthreads();
+    if (it >= cnt) return;
+    level_block<NT>(a, (int)order[first + it]);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1066,16 +1124,25 @@ __device__ void level_warp(const LevelArgs& a, const int seg) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_level_warp(LevelArgs a, const uint32_t* __restrict__ segs, int count) {
-  const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (w >= count) return;  // whole warps exit together
-  level_warp(a, (int)segs[w]);
+__global__ void __launch_bounds__(256) k_level_warp_q(LevelArgs a, const uint32_t* __restrict__ order, TierQueue* q) {
+  unsigned first, cnt;
+  tier_range(*q, 3, first, cnt);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(&q->next[3], 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= cnt) return;  // whole warps leave together
+    level_warp(a, (int)order[first + it]);
+  }
 }
 
 // segment sizes as descending sort keys, and the size-bin counts
 __global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int giant, int large, int small,
-                            uint32_t* __restrict__ key, uint32_t* __restrict__ val, unsigned* __restrict__ counts) {
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ val, unsigned* __restrict__ counts,
+                            unsigned* __restrict__ nseg_out) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g == 0) *nseg_out = (unsigned)nseg;
   if (g >= nseg) return;
   const uint32_t sz = seg_off[g + 1] - seg_off[g];
   key[g] = 0xffffffffu - sz;
@@ -1085,28 +1152,58 @@ __global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int 
   else if (sz <= (uint32_t)small) atomicAdd(&counts[2], 1u);
 }
 
-// global halo index of every member (or -1) and per-halo nucleus records
-__global__ void k_level_halo(const uint32_t* __restrict__ seg_off, const uint32_t* __restrict__ nnuc,
-                             const uint32_t* __restrict__ hbase, const int* __restrict__ eslot,
-                             const uint32_t* __restrict__ nuc_member, const long long* __restrict__ nuc_R2,
-                             int* __restrict__ ehalo, uint32_t* __restrict__ hnuc, long long* __restrict__ hR2,
-                             uint32_t* __restrict__ hseg) {
-  const int seg = blockIdx.x;
-  const unsigned base = seg_off[seg];
-  const int n = (int)(seg_off[seg + 1] - base);
-  const unsigned hb = hbase[seg];
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    int s = eslot[base + j];
-    ehalo[base + j] = s < 0 ? -1 : (int)(hb + s);
+// largest g with off[g] <= k (off ascending, off[0] = 0)
+__device__ __forceinline__ int seg_of(const uint32_t* __restrict__ off, int nseg, unsigned k) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= k) lo = mid;
+    else hi = mid - 1;
   }
-  for (int q = threadIdx.x; q < (int)nnuc[seg]; q += blockDim.x) {
-    hnuc[hb + q] = base + nuc_member[base + q];
-    hR2[hb + q] = nuc_R2[base + q];
-    hseg[hb + q] = seg;
-  }
+  return lo;
+}
+
+// global halo index of every member (or -1): one thread per member
+__global__ void k_level_halo_members(const uint32_t* __restrict__ seg_off, int nseg, const uint32_t* __restrict__ hbase,
+                                     const int* __restrict__ eslot, int* __restrict__ ehalo) {
+  const unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= seg_off[nseg]) return;
+  const int s = eslot[j];
+  ehalo[j] = s < 0 ? -1 : (int)(hbase[seg_of(seg_off, nseg, j)] + s);
+}
+
+// per-halo nucleus records: one thread per halo (halos of segment g start at
+// hbase[g])
+__global__ void k_level_halo_nuclei(const uint32_t* __restrict__ seg_off, int nseg, const uint32_t* __restrict__ hbase,
+                                    const uint32_t* __restrict__ nuc_member, const long long* __restrict__ nuc_R2,
+                                    uint32_t* __restrict__ hnuc, long long* __restrict__ hR2,
+                                    uint32_t* __restrict__ hseg) {
+  const unsigned h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= hbase[nseg]) return;
+  const int g = seg_of(hbase, nseg, h);  // hbase ascending; segments without nuclei repeat a value
+  const unsigned base = seg_off[g], q = h - hbase[g];
+  hnuc[h] = base + nuc_member[base + q];
+  hR2[h] = nuc_R2[base + q];
+  hseg[h] = (uint32_t)g;
 }
 
 }  // namespace
+
+// resident blocks per SM of the persistent level kernels (same for every
+// device of one build; queried once)
+static std::atomic<int> g_occ_l{0}, g_occ_m{0}, g_occ_w{0};
+
+void level_prepare() {
+  if (g_occ_l.load()) return;
+  int l = 0, m = 0, w = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l, k_level_q<1024>, 1024, 0) != cudaSuccess || l < 1) l = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_level_q<256>, 256, 0) != cudaSuccess || m < 1) m = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, k_level_warp_q, 256, 0) != cudaSuccess || w < 1) w = 1;
+  g_occ_m.store(m);
+  g_occ_w.store(w);
+  g_occ_l.store(l);
+  cso_sm_count();
+}
 
 int level_run(const LevelArgs& a, cudaStream_t st) {
   if (a.nseg <= 0) return CSO_OK;
@@ -1118,65 +1215,67 @@ int level_run(const LevelArgs& a, cudaStream_t st) {
 int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws, cudaStream_t st,
                       cudaStream_t side, cudaStream_t side2, cudaEvent_t fork, cudaEvent_t join,
                       cudaEvent_t join2, unsigned* host_counts) {
+  (void)host_counts;
   if (a.nseg <= 0) return CSO_OK;
   size_t mark = ws.off;
   uint32_t* key = ws.get<uint32_t>(a.nseg);
   uint32_t* val = ws.get<uint32_t>(a.nseg);
   uint32_t* key2 = ws.get<uint32_t>(a.nseg);
   uint32_t* val2 = ws.get<uint32_t>(a.nseg);
-  unsigned* counts = ws.get<unsigned>(4);
-  if (!key || !val || !key2 || !val2 || !counts) {
+  TierQueue* q = ws.get<TierQueue>(1);
+  if (!key || !val || !key2 || !val2 || !q) {
     cso_set_error("workspace exhausted in the batched schedule");
     return CSO_ERR_BUDGET;
   }
-  CSO_CUDA(cudaMemsetAsync(counts, 0, 4 * sizeof(unsigned), st));
+  CSO_CUDA(cudaMemsetAsync(q, 0, sizeof(TierQueue), st));
   k_seg_sizes<<<CL(cdiv(a.nseg, 256)), 256, 0, st>>>(a.seg_off, a.nseg, sc.giant, sc.large(), sc.small, key, val,
-                                                     counts);
+                                                     q->count, &q->nseg);
   // largest groups first: giants start at once, the rest fill in behind them
   uint32_t *pk = key, *pv = val;
   CSO_TRY(radix_sort_32(&pk, &pv, key2, val2, a.nseg, 32, ws, st));
-  CSO_CUDA(cudaMemcpyAsync(host_counts, counts, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  CSO_CUDA(cudaStreamSynchronize(st));
-  const int ng = (int)host_counts[0], nl = (int)host_counts[1], ns = (int)host_counts[2];
-  const int nm = a.nseg - ng - nl - ns;
-  // giants and large groups on their own streams, concurrent with the rest
-  if (ng > 0 || nl > 0) CSO_CUDA(cudaEventRecord(fork, st));
-  if (ng > 0) {
-    CSO_CUDA(cudaStreamWaitEvent(side, fork, 0));
-    k_level_cluster<<<CL(ng * CL_CS), CL_NT, 0, side>>>(a, pv);
-    CSO_CUDA(cudaGetLastError());
-  }
-  if (nl > 0) {
-    CSO_CUDA(cudaStreamWaitEvent(side2, fork, 0));
-    k_level<1024><<<CL(nl), 1024, 0, side2>>>(a, pv + ng);
-    CSO_CUDA(cudaGetLastError());
-  }
-  if (nm > 0) k_level<256><<<CL(nm), 256, 0, st>>>(a, pv + ng + nl);
-  if (ns > 0) k_level_warp<<<CL(cdiv(ns, 8)), 256, 0, st>>>(a, pv + ng + nl + nm, ns);
   CSO_CUDA(cudaGetLastError());
-  if (ng > 0) {
-    CSO_CUDA(cudaEventRecord(join, side));
-    CSO_CUDA(cudaStreamWaitEvent(st, join, 0));
-  }
-  if (nl > 0) {
-    CSO_CUDA(cudaEventRecord(join2, side2));
-    CSO_CUDA(cudaStreamWaitEvent(st, join2, 0));
-  }
+  // persistent grids sized to the device; blocks of a bin leave when its
+  // queue is empty
+  level_prepare();
+  const int occ_l = g_occ_l, occ_m = g_occ_m, occ_w = g_occ_w;
+  const int sms = cso_sm_count();
+  const int n_clusters = sms / CL_CS > 0 ? sms / CL_CS : 1;
+  const int nseg = a.nseg;
+  // no bin can hold more groups than there are: grids never exceed nseg
+  auto cap = [nseg](long long g) { return (unsigned)(g < nseg ? g : nseg); };
+  CSO_CUDA(cudaEventRecord(fork, st));
+  CSO_CUDA(cudaStreamWaitEvent(side, fork, 0));
+  k_level_cluster_q<<<CL(cap(n_clusters) * CL_CS), CL_NT, 0, side>>>(a, pv, q);
+  CSO_CUDA(cudaGetLastError());
+  CSO_CUDA(cudaStreamWaitEvent(side2, fork, 0));
+  k_level_q<1024><<<CL(cap((long long)sms * occ_l)), 1024, 0, side2>>>(a, pv, q, 1);
+  k_level_q<256><<<CL(cap((long long)sms * occ_m)), 256, 0, st>>>(a, pv, q, 2);
+  k_level_warp_q<<<CL(cdiv(cap((long long)sms * occ_w * 8), 8)), 256, 0, st>>>(a, pv, q);
+  CSO_CUDA(cudaGetLastError());
+  CSO_CUDA(cudaEventRecord(join, side));
+  CSO_CUDA(cudaStreamWaitEvent(st, join, 0));
+  CSO_CUDA(cudaEventRecord(join2, side2));
+  CSO_CUDA(cudaStreamWaitEvent(st, join2, 0));
   ws.off = mark;
   return CSO_OK;
 }
 
 int level_halo(int nseg, const uint32_t* seg_off, const uint32_t* nnuc, const uint32_t* hbase, const int* eslot,
                const uint32_t* nuc_member, const long long* nuc_R2, int* ehalo, uint32_t* hnuc, long long* hR2,
-               uint32_t* hseg, cudaStream_t st) {
+               uint32_t* hseg, long long n_members, long long n_halos, cudaStream_t st) {
+  (void)nnuc;
   if (nseg <= 0) return CSO_OK;
-  k_level_halo<<<CL(nseg), 256, 0, st>>>(seg_off, nnuc, hbase, eslot, nuc_member, nuc_R2, ehalo, hnuc, hR2, hseg);
+  if (n_members > 0)
+    k_level_halo_members<<<CL(cdiv(n_members, 256)), 256, 0, st>>>(seg_off, nseg, hbase, eslot, ehalo);
+  if (n_halos > 0)
+    k_level_halo_nuclei<<<CL(cdiv(n_halos, 256)), 256, 0, st>>>(seg_off, nseg, hbase, nuc_member, nuc_R2, hnuc, hR2,
+                                                                hseg);
   CSO_CUDA(cudaGetLastError());
   return CSO_OK;
 }
 
 PredConst make_pred_const(double K, long long u) {
-  PredConst c;
+  PredConst c{};  // zeroed padding: level stages are cached by their argument bytes
   c.K = K;
   int E;
   double f = frexp(K, &E);

@@ -55,9 +55,15 @@ struct LevelSchedule {
 };
 
 int level_run(const LevelArgs& a, cudaStream_t st);
+// one-time set-up of the batched schedule's launch sizes (occupancy queries),
+// kept out of stream capture
+void level_prepare();
 int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws, cudaStream_t st,
                       cudaStream_t side, cudaStream_t side2, cudaEvent_t fork, cudaEvent_t join,
                       cudaEvent_t join2, unsigned* host_counts);
+// ehalo[j] = global halo of member j (hbase[g] + its nucleus ordinal, or -1)
+// and the nucleus records of every halo; n_members = seg_off[nseg] and
+// n_halos = hbase[nseg] as the host knows them (launch sizes)
 int level_halo(int nseg, const uint32_t* seg_off, const uint32_t* nnuc, const uint32_t* hbase, const int* eslot,
                const uint32_t* nuc_member, const long long* nuc_R2, int* ehalo, uint32_t* hnuc, long long* hR2,
-               uint32_t* hseg, cudaStream_t st);
+               uint32_t* hseg, long long n_members, long long n_halos, cudaStream_t st);

@@ -360,6 +360,47 @@ int readback(cso_ctx* c, const void* dev, size_t bytes) {
 
 }  // namespace
 
+int level_stage(cso_ctx* c, const LevelArgs& L, const LevelSchedule& sched, unsigned* host_counts) {
+  cudaStream_t st = c->stream;
+  if (!(c->flags & CSO_FLAG_GRAPH))
+    return level_run_batched(L, sched, c->ws, st, c->side, c->side2, c->fork, c->join, c->join2, host_counts);
+  for (int i = 0; i < CSO_LEVEL_GRAPHS; ++i) {
+    LevelGraph& G = c->graphs[i];
+    if (G.exec && G.giant == sched.giant && G.small == sched.small && !memcmp(&G.args, &L, sizeof(LevelArgs))) {
+      ++c->graph_hits;
+      CSO_CUDA(cudaGraphLaunch(G.exec, st));
+      return CSO_OK;
+    }
+  }
+  // capture this stage (thread-local mode: the served path's other threads
+  // keep issuing work) and keep it in the oldest slot
+  level_prepare();
+  CSO_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const int rc = level_run_batched(L, sched, c->ws, st, c->side, c->side2, c->fork, c->join, c->join2, host_counts);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc != CSO_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  CSO_CUDA(e);
+  LevelGraph& G = c->graphs[c->graph_next];
+  c->graph_next = (c->graph_next + 1) % CSO_LEVEL_GRAPHS;
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CSO_CUDA(ei);
+  memcpy(&G.args, &L, sizeof(LevelArgs));
+  G.giant = sched.giant;
+  G.small = sched.small;
+  ++c->graph_captures;
+  CSO_CUDA(cudaGraphLaunch(G.exec, st));
+  return CSO_OK;
+}
+
 int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, Meta* meta, uint64_t* ol1,
                uint64_t* ol2, cso_halo** rows_out, int* nrows_out, uint32_t** rows_w_out, cso_radial** radial_out) {
   cudaStream_t st = c->stream;
@@ -506,8 +547,7 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   const bool batched = (c->flags & CSO_FLAG_BATCHED) != 0;
   const LevelSchedule sched = c->sched;
   unsigned* hcounts = (unsigned*)(c->pinned + 32);
-  if (batched)
-    CSO_TRY(level_run_batched(L1, sched, ws, st, c->side, c->side2, c->fork, c->join, c->join2, hcounts));
+  if (batched) CSO_TRY(level_stage(c, L1, sched, hcounts));
   else CSO_TRY(level_run(L1, st));
 
   // ---- prep2: L1 haloes, their members in key order, peaks within L1 ----
@@ -528,7 +568,7 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   ALLOC(uint32_t, hnuc, H1);
   ALLOC(long long, hR2, H1);
   ALLOC(uint32_t, hseg, H1);
-  CSO_TRY(level_halo(G, seg1, nnuc, hbase, eslot, nucm, nucR2, ehalo, hnuc, hR2, hseg, st));
+  CSO_TRY(level_halo(G, seg1, nnuc, hbase, eslot, nucm, nucR2, ehalo, hnuc, hR2, hseg, nd, H1, st));
   ALLOC(int, lab1, n);
   CSO_CUDA(cudaMemsetAsync(lab1, 0xff, sizeof(int) * n, st));
   ALLOC(uint32_t, akey, na);
@@ -575,8 +615,7 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   L2.nnuc = nnuc2;
   L2.work = &meta->work2;
   // edold / einel / ed are reused (na <= nd)
-  if (batched)
-    CSO_TRY(level_run_batched(L2, sched, ws, st, c->side, c->side2, c->fork, c->join, c->join2, hcounts));
+  if (batched) CSO_TRY(level_stage(c, L2, sched, hcounts));
   else CSO_TRY(level_run(L2, st));
 
   // ---- output ----
@@ -592,7 +631,7 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   ALLOC(long long, hR2b, H2);
   ALLOC(uint32_t, hseg2, H2);
   ALLOC(unsigned, h2size, H2);
-  CSO_TRY(level_halo(H1, seg2, nnuc2, hbase2, eslot2, nucm2, nucR22, ehalo2, hnuc2, hR2b, hseg2, st));
+  CSO_TRY(level_halo(H1, seg2, nnuc2, hbase2, eslot2, nucm2, nucR22, ehalo2, hnuc2, hR2b, hseg2, na, H2, st));
   if (H2 > 0) CSO_CUDA(cudaMemsetAsync(h2size, 0, sizeof(unsigned) * H2, st));
 
   if (ol1 && nd > 0) k_out_l1<<<G1(nd)>>>(ehalo, nd, gs, spos, hnuc, eid, ol1);

@@ -23,6 +23,15 @@ struct ServedRequest {
 };
 struct ServedState;
 
+// a captured level stage of the batched schedule, keyed by its launch
+// arguments (the same box gives the same workspace offsets, hence the key)
+struct LevelGraph {
+  LevelArgs args;
+  int giant = 0, small = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+#define CSO_LEVEL_GRAPHS 4
+
 struct cso_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -45,7 +54,14 @@ struct cso_ctx {
   LevelSchedule sched;            // size bins of the batched schedule (cso_autotune)
   double level_ms = 0;            // device time of the last call's CompaSO levels
   ServedState* served = nullptr;  // created by the first cso_submit
+  LevelGraph graphs[CSO_LEVEL_GRAPHS];  // CSO_FLAG_GRAPH: captured level stages
+  int graph_next = 0;
+  long long graph_hits = 0, graph_captures = 0;
 };
+
+// The batched level stage; with CSO_FLAG_GRAPH captured once per distinct
+// argument set and replayed as a CUDA graph.
+int level_stage(cso_ctx* c, const LevelArgs& L, const LevelSchedule& sched, unsigned* host_counts);
 
 struct Meta {  // device counters read back by the host
   unsigned long long sigma_max, id_max;

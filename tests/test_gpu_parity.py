@@ -432,3 +432,24 @@ def test_cluster_path_select_stress():
             assert_same(g, o)
     finally:
         c.close()
+
+
+def test_batched_level_stages_as_cuda_graphs():
+    """CSO_FLAG_GRAPH: the level stages captured once and replayed give the
+    oracle's results on every call (a capture, then replays of it)."""
+    pos, ids, meta = synth.tiny()
+    p, po = both_params(U64)
+    o = O.find_groups(pos, ids, po)
+    c = cso.Context(0, flags=cso.FLAG_BATCHED | cso.FLAG_GRAPH)
+    try:
+        dpos = torch.from_numpy(pos).cuda()
+        dids = torch.from_numpy(ids.view(np.int64)).cuda()
+        for _ in range(3):
+            g = c.find_groups(dpos, dids, p)
+            assert_same(g, o)
+        # another box in the same context: a new capture, same parity
+        pos2, ids2, _ = synth.patch(extent=16.0, lo=-8.0, seed=2)
+        g2, o2 = run_both(c, pos2, ids2)
+        assert_same(g2, o2)
+    finally:
+        c.close()
