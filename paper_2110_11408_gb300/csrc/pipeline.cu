@@ -255,43 +255,62 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long* sh) {
   return t;
 }
 
-// one block per L1 halo: statistics over its members (the L2-level segment)
-__global__ void __launch_bounds__(256) k_summary(
-    const uint32_t* __restrict__ seg2, const int4* __restrict__ epos2, const int* __restrict__ ehalo2,
-    const uint32_t* __restrict__ ek2, const uint32_t* __restrict__ hnuc, const long long* __restrict__ hR2,
-    const int4* __restrict__ epos, const uint64_t* __restrict__ eid, const uint32_t* __restrict__ gs,
-    const int* __restrict__ root, const unsigned long long* __restrict__ minid, const uint32_t* __restrict__ nnuc2,
-    const uint32_t* __restrict__ hbase2, const uint32_t* __restrict__ hnuc2, const unsigned* __restrict__ h2size,
-    double inv_u, int np_min, int x0, cso_halo* __restrict__ rows, uint32_t* __restrict__ keep) {
-  __shared__ long long sh[8];
-  const int h = blockIdx.x;
-  const unsigned b = seg2[h];
-  const int n = (int)(seg2[h + 1] - b);
+// Statistics of every L1 halo over its members (the L2-level segments).
+// Pass one, one thread per member: the minimum-image offsets of the member
+// from its halo's nucleus, and from the halo's first L2 nucleus for members
+// of that L2 halo, summed exactly per halo in int64 (lanes of a warp that
+// share a halo add once); pass two, one thread per halo, forms the row.
+__global__ void k_summary_sums(const uint32_t* __restrict__ ehal2, int na, const int4* __restrict__ epos2,
+                               const int* __restrict__ ehalo2, const uint32_t* __restrict__ hnuc,
+                               const int4* __restrict__ epos, const uint32_t* __restrict__ nnuc2,
+                               const uint32_t* __restrict__ hbase2, const uint32_t* __restrict__ hnuc2,
+                               unsigned long long* __restrict__ acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool v = i < na;
+  const int h = v ? (int)ehal2[i] : -1;
+  long long s[6] = {0, 0, 0, 0, 0, 0};
+  if (v) {
+    const int4 q = epos2[i];
+    const int4 pn = epos[hnuc[h]];
+    s[0] = mi(q.x - pn.x);
+    s[1] = mi(q.y - pn.y);
+    s[2] = mi(q.z - pn.z);
+    if (nnuc2[h] > 0 && ehalo2[i] == (int)hbase2[h]) {
+      const int4 p2 = epos2[hnuc2[hbase2[h]]];
+      s[3] = mi(q.x - p2.x);
+      s[4] = mi(q.y - p2.y);
+      s[5] = mi(q.z - p2.z);
+    }
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, h);
+  const int leader = __ffs(peers) - 1;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    long long t = 0;
+    for (unsigned m = peers; m; m &= m - 1) t += __shfl_sync(peers, s[k], __ffs(m) - 1);
+    if (v && (int)(threadIdx.x & 31) == leader && t) atomicAdd(&acc[6 * (size_t)h + k], (unsigned long long)t);
+  }
+}
+
+__global__ void k_summary(const uint32_t* __restrict__ seg2, int H1, const int4* __restrict__ epos2,
+                          const uint32_t* __restrict__ hnuc, const long long* __restrict__ hR2,
+                          const int4* __restrict__ epos, const uint64_t* __restrict__ eid,
+                          const uint32_t* __restrict__ gs, const int* __restrict__ root,
+                          const unsigned long long* __restrict__ minid, const uint32_t* __restrict__ nnuc2,
+                          const uint32_t* __restrict__ hbase2, const uint32_t* __restrict__ hnuc2,
+                          const unsigned* __restrict__ h2size, const unsigned long long* __restrict__ acc,
+                          const uint32_t* __restrict__ ek2, double inv_u, int np_min, int x0,
+                          cso_halo* __restrict__ rows, uint32_t* __restrict__ keep) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H1) return;
+  const int n = (int)(seg2[h + 1] - seg2[h]);
   const uint32_t kn = hnuc[h];
   const int4 pn = epos[kn];
   const int nl2 = (int)nnuc2[h];
   const int first2 = (int)hbase2[h];
-  int4 p2 = pn;
-  if (nl2 > 0) p2 = epos2[hnuc2[first2]];
-  long long sx = 0, sy = 0, sz = 0, tx = 0, ty = 0, tz = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    int4 q = epos2[b + i];
-    sx += mi(q.x - pn.x);
-    sy += mi(q.y - pn.y);
-    sz += mi(q.z - pn.z);
-    if (nl2 > 0 && ehalo2[b + i] == first2) {
-      tx += mi(q.x - p2.x);
-      ty += mi(q.y - p2.y);
-      tz += mi(q.z - p2.z);
-    }
-  }
-  sx = block_sum_ll(sx, sh);
-  sy = block_sum_ll(sy, sh);
-  sz = block_sum_ll(sz, sh);
-  tx = block_sum_ll(tx, sh);
-  ty = block_sum_ll(ty, sh);
-  tz = block_sum_ll(tz, sh);
-  if (threadIdx.x != 0) return;
+  const long long sx = (long long)acc[6 * (size_t)h], sy = (long long)acc[6 * (size_t)h + 1],
+                  sz = (long long)acc[6 * (size_t)h + 2], tx = (long long)acc[6 * (size_t)h + 3],
+                  ty = (long long)acc[6 * (size_t)h + 4], tz = (long long)acc[6 * (size_t)h + 5];
   cso_halo r;
   r.nucleus_id = eid[kn];
   r.N = n;
@@ -304,6 +323,7 @@ __global__ void __launch_bounds__(256) k_summary(
   r.n_l2 = nl2;
   for (int k = 0; k < 5; ++k) r.l2_top5_N[k] = 0;
   if (nl2 > 0) {
+    const int4 p2 = epos2[hnuc2[first2]];
     long long n2 = h2size[first2];
     r.l2max_id = eid[ek2[hnuc2[first2]]];
     r.l2max_N = n2;
@@ -654,8 +674,14 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
   ALLOC(uint32_t, keep, H1 + 1);
   int nrows = 0;
   if (H1 > 0) {
-    k_summary<<<CL(H1), 256, 0, st>>>(seg2, epos2, ehalo2, ek2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2,
-                                   h2size, 1.0 / p->l_mean_grid, p->np_min_L1, gi.x0, rows, keep);
+    {
+      ALLOC(unsigned long long, acc, 6 * (size_t)H1);
+      CSO_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 6 * (size_t)H1, st));
+      if (na > 0)
+        k_summary_sums<<<G1(na)>>>(ehal2, na, epos2, ehalo2, hnuc, epos, nnuc2, hbase2, hnuc2, acc);
+      k_summary<<<G1(H1)>>>(seg2, H1, epos2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2, h2size,
+                            acc, ek2, 1.0 / p->l_mean_grid, p->np_min_L1, gi.x0, rows, keep);
+    }
     CSO_CUDA(cudaGetLastError());
     cso_radial* rad = nullptr;
     if (radial_out) {
