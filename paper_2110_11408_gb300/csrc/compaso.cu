@@ -453,21 +453,31 @@ __device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
     const int x1 = __shfl_sync(0xffffffffu, qx1, r), y = __shfl_sync(0xffffffffu, qy, r);
     const int z = __shfl_sync(0xffffffffu, qz, r);
     const uint32_t n0 = h0 - l0, tot = n0 + (h1 - l1);
-    for (uint32_t f0 = 0; f0 < tot; f0 += 32) {
-      const uint32_t f = f0 + lane;
+    // four neighbours per lane per step: every load of the step is issued
+    // before any comparison, so a step costs one memory round trip, not four
+    constexpr int U = 4;
+    for (uint32_t f0 = 0; f0 < tot; f0 += 32 * U) {
+      int4 q[U];
+      int lab[U];
+      long long st[U];
+      uint32_t tt[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const uint32_t f = f0 + k * 32 + lane;
+        tt[k] = f < tot ? (f < n0 ? l0 + f : l1 + (f - n0)) : se;
+        q[k] = a.spos[tt[k]];
+        lab[k] = a.slab[tt[k]];
+        st[k] = a.ssig[tt[k]];
+      }
       bool beat = false;
-      if (f < tot) {
-        const uint32_t t = f < n0 ? l0 + f : l1 + (f - n0);
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const uint32_t f = f0 + k * 32 + lane;
+        if (tt[k] == se || lab[k] != glabel) continue;  // past the end (tt = se), self, or another group
         const int qx = f < n0 ? p.x : x1;
-        if (t != se) {
-          const int4 q = a.spos[t];
-          const int dx = qx - q.x, dy = y - q.y, dz = z - q.z;
-          const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-          if (d < a.b2 && a.slab[t] == glabel) {
-            const long long st = a.ssig[t];
-            beat = st > sp || (st == sp && a.sid[t] < idp);
-          }
-        }
+        const int dx = qx - q[k].x, dy = y - q[k].y, dz = z - q[k].z;
+        const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+        if (d < a.b2) beat = beat || st[k] > sp || (st[k] == sp && a.sid[tt[k]] < idp);
       }
       if (__any_sync(0xffffffffu, beat)) return false;
     }
