@@ -14,60 +14,160 @@
 
 namespace {
 
-__global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, CellGrid g, uint32_t* __restrict__ key,
-                             uint32_t* __restrict__ rank, uint32_t* __restrict__ count, int* __restrict__ bad) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// Table cell of input particle i under the rules of k_cell_count: a position
+// outside the box counts as (0, 0, 0) and a window particle outside the
+// window's columns is filed under table column 0 with y = z = 0 (both set
+// *bad_code).
+__device__ __forceinline__ uint32_t bin_key(const int32_t* __restrict__ pos, size_t i, const CellGrid& g,
+                                            int* bad_code) {
   int x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  *bad_code = 0;
   if ((unsigned)x >= (unsigned)CSO_BOX || (unsigned)y >= (unsigned)CSO_BOX || (unsigned)z >= (unsigned)CSO_BOX) {
-    atomicExch(bad, 1);
+    *bad_code = 1;
     x = y = z = 0;
   }
   // table column from the grid x (whole box or window alike)
   int tc = g.colmap ? g.colmap[cell_coord(x, g.nc)] : cell_coord(x, g.nc);
-  if (tc < 0) {  // a window particle outside the window's columns: filed under cell 0 like the rest
-    atomicExch(bad, 2);
+  if (tc < 0) {
+    *bad_code = 2;
     tc = 0;
     y = z = 0;
   }
-  const uint32_t k = (uint32_t)grid_cell(g, cell_coord(z, g.nc), cell_coord(y, g.nc), tc);
-  key[i] = k;
-  rank[i] = atomicAdd(&count[k], 1u);
+  return (uint32_t)grid_cell(g, cell_coord(z, g.nc), cell_coord(y, g.nc), tc);
 }
 
-// Slot of every particle: only the 4-byte input index is scattered (perm);
-// the positions and ids follow by a gather in slot order, so the 24 bytes a
-// particle carries are read from scattered places and written in sequence
-// (scattered writes of partial sectors cost a sector read each).
-__global__ void k_cell_scatter(long long n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
-                               const uint32_t* __restrict__ start, uint32_t* __restrict__ perm,
-                               uint32_t* __restrict__ inv) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t dst = start[key[i]] + rank[i];
-  perm[dst] = (uint32_t)i;
-  if (inv) inv[i] = dst;
-}
-
-// A particle that k_cell_count rejected (outside the box, or outside a
-// window's columns) was filed under table cell 0; it is stored at that cell's
-// low corner so that every later kernel derives an in-range cell from it.  The
-// request still fails (the bad flag), but no kernel indexes past the table.
-__global__ void k_cell_gather(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n,
-                              CellGrid g, const uint32_t* __restrict__ perm, int4* __restrict__ spos,
-                              uint64_t* __restrict__ sid) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const uint32_t i = perm[t];
-  int x = pos[3 * (size_t)i], y = pos[3 * (size_t)i + 1], z = pos[3 * (size_t)i + 2];
+// Stored position of input particle i: x relative to the table's x0 (a
+// window never wraps), y, z, and w = i.  A particle that k_cell_count
+// rejected is stored at the low corner of table column 0, so every later
+// kernel derives an in-range cell from it (the request still fails on the bad
+// flag, but no kernel indexes past the table).
+__device__ __forceinline__ int4 stored_pos(const int32_t* __restrict__ pos, size_t i, const CellGrid& g) {
+  int x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
   const bool out = (unsigned)x >= (unsigned)CSO_BOX || (unsigned)y >= (unsigned)CSO_BOX ||
                    (unsigned)z >= (unsigned)CSO_BOX || (g.colmap && g.colmap[cell_coord(x, g.nc)] < 0);
   if (out) {
     x = g.colmap ? cell_lo(g.cols[0], g.nc) : 0;
     y = z = 0;
   }
-  spos[t] = make_int4((x - g.x0) & (CSO_BOX - 1), y, z, (int)i);
-  sid[t] = ids[i];
+  return make_int4((x - g.x0) & (CSO_BOX - 1), y, z, (int)i);
+}
+
+// Cells are sorted by x (k_cell_place), so a run of adjacent x cells is
+// sorted by stored x: trim [lo, hi) to the neighbours with xl <= x <= xh by
+// two binary searches in lockstep.
+__device__ __forceinline__ void x_trim(const int4* __restrict__ spos, uint32_t& lo, uint32_t& hi, int xl, int xh) {
+  uint32_t a = lo, b = hi, c = lo, d = hi;
+  while (a < b || c < d) {
+    if (a < b) {
+      const uint32_t m = (a + b) >> 1;
+      if (spos[m].x < xl) a = m + 1; else b = m;
+    }
+    if (c < d) {
+      const uint32_t m = (c + d) >> 1;
+      if (spos[m].x <= xh) c = m + 1; else d = m;
+    }
+  }
+  lo = a;
+  hi = c > a ? c : a;
+}
+
+__global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, CellGrid g, uint32_t* __restrict__ key,
+                             uint32_t* __restrict__ rank, uint32_t* __restrict__ count, int* __restrict__ bad) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int code;
+  const uint32_t k = bin_key(pos, (size_t)i, g, &code);
+  if (code) atomicExch(bad, code);
+  key[i] = k;
+  rank[i] = atomicAdd(&count[k], 1u);
+}
+
+// What k_cell_place needs of the particle at a provisional slot: its sort
+// key (stored x << 32 | input index) and its cell's range, so that the
+// placement reads neither the positions' cells nor the table again.
+struct __align__(16) BinRec {
+  unsigned long long key;
+  uint32_t c0, m;
+};
+
+// Provisional slot of every particle (cell start + arrival rank): only the
+// 16-byte record is scattered (one sector either way), and inv (optional)
+// receives the provisional slot in input order.
+__global__ void k_cell_scatter(const int32_t* __restrict__ pos, long long n, CellGrid g,
+                               const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+                               const uint32_t* __restrict__ start, BinRec* __restrict__ rec,
+                               uint32_t* __restrict__ inv) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int4 q = stored_pos(pos, (size_t)i, g);
+  const uint32_t k = key[i], c0 = start[k], c1 = start[k + 1];
+  const uint32_t p = c0 + rank[i];
+  BinRec r;
+  r.key = ((unsigned long long)(unsigned)q.x << 32) | (unsigned long long)i;
+  r.c0 = c0;
+  r.m = c1 - c0;
+  rec[p] = r;
+  if (inv) inv[i] = p;
+}
+
+// Final slot of every particle: its cell's start plus its rank by (stored x,
+// input index) among the cell's particles, so every cell, and with it every
+// (y, z) row of adjacent x cells, is sorted by x (the density pass bounds its
+// runs by x).  A lane counts a cell of up to 32 particles alone; the warp
+// streams each larger cell once through shared memory for all its lanes in
+// that cell.  The positions and ids are read from their scattered input
+// places and written into the cell's range; fin (optional) maps the
+// provisional slot to the final one (k_cell_inv composes it into inv).
+constexpr int PLACE_SMALL = 32;
+__global__ void __launch_bounds__(256) k_cell_place(const int32_t* __restrict__ pos,
+                                                    const uint64_t* __restrict__ ids, long long n, CellGrid g,
+                                                    const BinRec* __restrict__ rec, int4* __restrict__ spos,
+                                                    uint64_t* __restrict__ sid, uint32_t* __restrict__ fin) {
+  __shared__ unsigned long long tile[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = t < n;
+  unsigned long long kt = 0;
+  uint32_t c0 = 0, c1 = 0;
+  if (act) {
+    const BinRec r = rec[t];
+    kt = r.key;
+    c0 = r.c0;
+    c1 = r.c0 + r.m;
+  }
+  const bool big = act && c1 - c0 > (uint32_t)PLACE_SMALL;
+  uint32_t rk = 0;
+  if (act && !big)
+    for (uint32_t u = c0; u < c1; ++u) rk += rec[u].key < kt;
+  unsigned pend = __ballot_sync(0xffffffffu, big);
+  while (pend) {
+    const int L = __ffs(pend) - 1;
+    const uint32_t b0 = __shfl_sync(0xffffffffu, c0, L), b1 = __shfl_sync(0xffffffffu, c1, L);
+    const bool mine = big && c0 == b0;
+    for (uint32_t u0 = b0; u0 < b1; u0 += 32) {
+      tile[w][lane] = u0 + lane < b1 ? rec[u0 + lane].key : ~0ull;  // past the cell: never below a key
+      __syncwarp();
+      if (mine) {
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) rk += tile[w][k] < kt;
+      }
+      __syncwarp();
+    }
+    pend &= ~__ballot_sync(0xffffffffu, mine);
+  }
+  if (!act) return;
+  const uint32_t i = (uint32_t)kt;
+  const uint32_t d = c0 + rk;
+  spos[d] = stored_pos(pos, i, g);
+  sid[d] = ids[i];
+  if (fin) fin[t] = d;
+}
+
+// inv[i] = fin[inv[i]]: the final slot of every input particle (a gather in
+// input order instead of a scattered write from the placement)
+__global__ void k_cell_inv(long long n, const uint32_t* __restrict__ fin, uint32_t* __restrict__ inv) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) inv[i] = fin[inv[i]];
 }
 
 __device__ __forceinline__ uint32_t kern(int4 q, int xq, int yq, int zq, uint32_t b2) {
@@ -246,7 +346,7 @@ __device__ __forceinline__ void run_bounds(const WarpRows& R, int r, uint32_t& l
 
 template <bool SMALL>
 __global__ void __launch_bounds__(DENS_WARPS * 32, 4) k_density(CellGrid g, const int4* __restrict__ spos, int n,
-                                                                 uint32_t b2, int include_self,
+                                                                 uint32_t b2, int reach, int include_self,
                                                                  long long* __restrict__ sigma,
                                                                  const uint8_t* __restrict__ only,
                                                                  const uint32_t* __restrict__ order, int max_span) {
@@ -258,9 +358,19 @@ __global__ void __launch_bounds__(DENS_WARPS * 32, 4) k_density(CellGrid g, cons
   const int4 p = s < n ? spos[s] : make_int4(0, 0, 0, 0);
   const unsigned vmask = __ballot_sync(0xffffffffu, valid);
   if (!vmask) return;
-  const WarpRows R = warp_rows(g, p, valid, vmask, lane, max_span);
+  WarpRows R = warp_rows(g, p, valid, vmask, lane, max_span);
   unsigned long long acc = 0;
   if (R.uniform) {
+    // keep the neighbours within reach (the largest e with e^2 < b2) of the
+    // warp's x extent in x: a neighbour farther out in x is farther than b
+    // from every query of the warp
+    const int xmin = __reduce_min_sync(0xffffffffu, valid ? p.x : INT_MAX);
+    const int xmax = __reduce_max_sync(0xffffffffu, valid ? p.x : INT_MIN);
+    if (lane < 9) {
+      // neighbour image x = stored x - shift
+      if (R.hi0 - R.lo0 > 16u) x_trim(spos, R.lo0, R.hi0, xmin - reach, xmax + reach);
+      if (R.hi1 - R.lo1 > 16u) x_trim(spos, R.lo1, R.hi1, xmin - reach + R.sx1, xmax + reach + R.sx1);
+    }
     const int ox = __shfl_sync(0xffffffffu, p.x, R.src), oy = __shfl_sync(0xffffffffu, p.y, R.src),
               oz = __shfl_sync(0xffffffffu, p.z, R.src);
     const int qx = p.x - ox, qy = p.y - oy, qz = p.z - oz;
@@ -585,7 +695,7 @@ __global__ void k_straggler_list(const uint32_t* __restrict__ sscan, const int* 
 // memory and stops at the first link, so a pair of dense cells costs one
 // tile instead of a test per particle.
 __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __restrict__ spos, int s0,
-                                               uint32_t lfof2, int* __restrict__ parent,
+                                               uint32_t lfof2, int lreach, int* __restrict__ parent,
                                                const int* __restrict__ cell_root, const uint8_t* __restrict__ strag,
                                                int4* tile, int* tmain, int4* tileA, int* hit, int lane) {
   const int4 p0 = spos[s0];
@@ -678,19 +788,34 @@ __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __
     if (lane == 0) same = uf_root(parent, crA) == uf_root(parent, cb);
     if (__shfl_sync(0xffffffffu, same, 0)) continue;
     bool found = false;
-    for (uint32_t a0 = a_lo; a0 < a_hi && !found; a0 += 32) {
+    // only our slots within l_FoF in x of the neighbour's x extent can link
+    uint32_t ta = a_lo, tb = a_hi;
+    if (lane == 0 && tb - ta > 32u) {
+      const int bx0 = spos[lo].x - sx, bx1 = spos[hi - 1].x - sx;
+      x_trim(spos, ta, tb, bx0 - lreach, bx1 + lreach);
+    }
+    ta = __shfl_sync(0xffffffffu, ta, 0);
+    tb = __shfl_sync(0xffffffffu, tb, 0);
+    for (uint32_t a0 = ta; a0 < tb && !found; a0 += 32) {
       const uint32_t a = a0 + lane;
-      const bool av = a < a_hi && parent[a] >= 0 && !strag[a];
+      const bool av = a < tb && parent[a] >= 0 && !strag[a];
       const int4 pa = av ? spos[a] : make_int4(0, 0, 0, 0);
       const int xq = pa.x + sx, yq = pa.y + sy, zq = pa.z + sz;
       if (!__any_sync(0xffffffffu, av)) continue;
-      for (uint32_t b0 = lo; b0 < hi; b0 += 32) {
+      // the neighbour's slots within l_FoF of this tile in x (cells are sorted by x)
+      const int xqmin = __reduce_min_sync(0xffffffffu, av ? xq : INT_MAX);
+      const int xqmax = __reduce_max_sync(0xffffffffu, av ? xq : INT_MIN);
+      uint32_t blo = lo, bhi = hi;
+      if (lane == 0 && bhi - blo > 32u) x_trim(spos, blo, bhi, xqmin - lreach, xqmax + lreach);
+      blo = __shfl_sync(0xffffffffu, blo, 0);
+      bhi = __shfl_sync(0xffffffffu, bhi, 0);
+      for (uint32_t b0 = blo; b0 < bhi; b0 += 32) {
         const uint32_t t = b0 + lane;
-        const bool tv = t < hi && parent[t] >= 0 && !strag[t];
+        const bool tv = t < bhi && parent[t] >= 0 && !strag[t];
         tile[lane] = tv ? spos[t] : make_int4(0, 0, 0, 0);
         tmain[lane] = tv;
         __syncwarp();
-        const int m = hi - b0 < 32 ? (int)(hi - b0) : 32;
+        const int m = bhi - b0 < 32 ? (int)(bhi - b0) : 32;
         bool found_here = false;
         if (av) {
           for (int k = 0; k < m; ++k) {
@@ -718,7 +843,7 @@ __device__ __forceinline__ void fof_cell_pairs(const CellGrid& g, const int4* __
 
 __global__ void __launch_bounds__(256) k_fof_cells(CellGrid g, const int4* __restrict__ spos,
                                                    const int* __restrict__ clist, const uint32_t* __restrict__ ncl_ptr,
-                                                   uint32_t lfof2, int* __restrict__ parent,
+                                                   uint32_t lfof2, int lreach, int* __restrict__ parent,
                                                    const int* __restrict__ cell_root,
                                                    const uint8_t* __restrict__ strag) {
   __shared__ int4 tile[8][32];
@@ -728,7 +853,8 @@ __global__ void __launch_bounds__(256) k_fof_cells(CellGrid g, const int4* __res
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int ncl = (int)*ncl_ptr;
   for (int wi = blockIdx.x * 8 + w; wi < ncl; wi += gridDim.x * 8)
-    fof_cell_pairs(g, spos, clist[wi], lfof2, parent, cell_root, strag, tile[w], tmain[w], tileA[w], hit[w], lane);
+    fof_cell_pairs(g, spos, clist[wi], lfof2, lreach, parent, cell_root, strag, tile[w], tmain[w], tileA[w], hit[w],
+                   lane);
 }
 
 // Pass three, the stragglers one by one (a list of them): against every neighbour cell in
@@ -739,7 +865,8 @@ __global__ void __launch_bounds__(256) k_fof_cells(CellGrid g, const int4* __res
 __global__ void __launch_bounds__(256) k_fof_stragglers(CellGrid g, const int4* __restrict__ spos,
                                                         const int* __restrict__ didx,
                                                         const uint32_t* __restrict__ nd_ptr, uint32_t lfof2,
-                                                        int* __restrict__ parent, const int* __restrict__ cell_root,
+                                                        int lreach, int* __restrict__ parent,
+                                                        const int* __restrict__ cell_root,
                                                         const uint8_t* __restrict__ strag,
                                                         const uint2* __restrict__ srange) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -776,9 +903,12 @@ __global__ void __launch_bounds__(256) k_fof_stragglers(CellGrid g, const int4* 
         const int cm = cell_root[c_lo];
         if (cm == CELL_EMPTY) continue;
         const int xq = p.x + xsh[k], yq = p.y + sy, zq = p.z + sz;
-        // the main tree: the first link joins all of it
+        // the main tree: the first link joins all of it (only the cell's
+        // slots within l_FoF in x can link; cells are sorted by x)
         if (uf_root(parent, cm) != rs) {
-          for (uint32_t t = c_lo; t < c_hi; ++t) {
+          uint32_t t0 = c_lo, t1 = c_hi;
+          if (t1 - t0 > 16u) x_trim(spos, t0, t1, xq - lreach, xq + lreach);
+          for (uint32_t t = t0; t < t1; ++t) {
             const int pt = parent[t];
             if (pt < 0 || strag[t]) continue;
             const int4 q = spos[t];
@@ -830,6 +960,15 @@ __global__ void k_fof_finish(int* __restrict__ parent, int n, const long long* _
 
 }  // namespace
 
+// the largest e >= 0 with e^2 < v (v >= 1): the farthest x offset at which
+// a pair can still be closer than sqrt(v)
+static int reach_below(long long v) {
+  long long e = (long long)sqrt((double)v);
+  while (e > 0 && e * e >= v) --e;
+  while ((e + 1) * (e + 1) < v) ++e;
+  return (int)e;
+}
+
 int cells_choose(long long b2, int* nc_out) {
   // largest nc with (2^21 / nc)^2 >= b2: cells at least as wide as b
   double b = sqrt((double)b2);
@@ -861,10 +1000,14 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
               int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st, uint32_t* inv) {
   long long ncell = (long long)g.ncols * g.nc * g.nc;
   size_t mark = ws.off;
-  uint32_t* key = ws.get<uint32_t>(n);
-  uint32_t* rank = ws.get<uint32_t>(n);
-  uint32_t* perm = ws.get<uint32_t>(n);
-  if (!key || !rank || !perm) {
+  // the cell keys and arrival ranks live in the output spos (16 bytes per
+  // particle) until k_cell_place overwrites it; the records (and the slot map
+  // when inv is wanted) take workspace
+  uint32_t* key = reinterpret_cast<uint32_t*>(spos);
+  uint32_t* rank = key + n;
+  BinRec* rec = ws.get<BinRec>(n);
+  uint32_t* fin = inv ? ws.get<uint32_t>(n) : nullptr;
+  if (!rec || (inv && !fin)) {
     cso_set_error("workspace exhausted in binning");
     return CSO_ERR_BUDGET;
   }
@@ -875,8 +1018,11 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
   }
   CSO_TRY(scan_u32(start, ncell + 1, nullptr, ws, st));
   if (n > 0) {
-    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(n, key, rank, start, perm, inv);
-    k_cell_gather<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, g, perm, spos, sid);
+    CellGrid gs = g;
+    gs.start = start;
+    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, n, gs, key, rank, start, rec, inv);
+    k_cell_place<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, gs, rec, spos, sid, fin);
+    if (inv) k_cell_inv<<<CL(cdiv(n, 256)), 256, 0, st>>>(n, fin, inv);
     CSO_CUDA(cudaGetLastError());
   }
   ws.off = mark;
@@ -914,13 +1060,16 @@ int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int i
   int max_span;
   bool small;
   density_span(g.nc, &max_span, &small);
+  const int reach = reach_below(b2);
   CSO_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * DENS_CLASSES, st));
   k_density_cost<<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, only, max_span, cls, rank, counts);
   k_density_order<<<CL(cdiv(nb, 256)), 256, 0, st>>>(cls, rank, counts, nb, order);
   if (small)
-    k_density<true><<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only, order, max_span);
+    k_density<true><<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, reach, include_self, sigma, only, order,
+                                                         max_span);
   else
-    k_density<false><<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, include_self, sigma, only, order, max_span);
+    k_density<false><<<CL(nb), DENS_WARPS * 32, 0, st>>>(g, spos, n, b2, reach, include_self, sigma, only, order,
+                                                          max_span);
   if (pairs) k_count_pairs<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, n, b2, pairs);
   CSO_CUDA(cudaGetLastError());
   ws.off = mark;
@@ -965,8 +1114,9 @@ int cells_fof(const CellGrid& g, const int4* spos, int n, const long long* sigma
   k_straggler_list<<<CL(cdiv(n, 256)), 256, 0, st>>>(sflag, didx, nd, slist);
   k_straggler_ranges<<<CL(cdiv(n, 256)), 256, 0, st>>>(spos, g, slist, sflag + n, srange);
   // pass two: main trees of adjacent cells; pass three: stragglers
-  k_fof_cells<<<CL(cso_sm_count() * 8), 256, 0, st>>>(g, spos, clist, ncl, lfof2, parent, cell_root, strag);
-  k_fof_stragglers<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, slist, sflag + n, lfof2, parent, cell_root, strag,
+  const int lreach = reach_below(lfof2);
+  k_fof_cells<<<CL(cso_sm_count() * 8), 256, 0, st>>>(g, spos, clist, ncl, lfof2, lreach, parent, cell_root, strag);
+  k_fof_stragglers<<<CL(cdiv(n, 256)), 256, 0, st>>>(g, spos, slist, sflag + n, lfof2, lreach, parent, cell_root, strag,
                                                      srange);
   CSO_CUDA(cudaMemsetAsync(minid, 0xff, sizeof(unsigned long long) * n, st));
   k_fof_finish<<<CL(cdiv(n, 256)), 256, 0, st>>>(parent, n, sigma, T_L0, sid, root, minid);

@@ -119,8 +119,11 @@ int cells_choose(long long b2, int* nc_out);
 // the x columns holding resident particles.
 #define CSO_MAX_DENSE_NC 1290
 int cells_check_dense(int nc);
-// Counting sort of the particles into the cell table; inv (optional, n
-// entries) receives the sorted slot of every input particle.
+// Counting sort of the particles into the cell table, each cell ordered by
+// (stored x, input index), so the x cells of a row form one run sorted by x;
+// inv (optional, n entries) receives the sorted slot of every input particle.
+// spos doubles as scratch for the cell keys and arrival ranks (it must not
+// alias pos).
 int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGrid& g, uint32_t* start,
               int4* spos, uint64_t* sid, int* bad, Workspace& ws, cudaStream_t st, uint32_t* inv = nullptr);
 int cells_density(const CellGrid& g, const int4* spos, int n, uint32_t b2, int include_self, long long* sigma,

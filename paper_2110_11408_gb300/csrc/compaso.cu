@@ -213,6 +213,25 @@ __device__ __forceinline__ int first_bin(unsigned long long d, const PredConst& 
 }
 
 // R^2 of nucleus pc over the n members at epos[0..n); distances left in ed.
+// The bin's smallest and largest distance.  A bound read without the atomic
+// can only be stale in the safe direction (the minimum only falls, the
+// maximum only rises), so a member that does not beat it is skipped: per bin
+// only the few members that move a bound pay a 64-bit shared atomic, not
+// every member.
+__device__ __forceinline__ void bin_minmax(SelShared& S, int b, unsigned long long d) {
+  if (d < *(volatile unsigned long long*)&S.dmn[b]) atomicMin(&S.dmn[b], d);
+  if (d > *(volatile unsigned long long*)&S.dmx[b]) atomicMax(&S.dmx[b], d);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+    v = t > v ? t : v;
+  }
+  return v;
+}
+
 template <int NT>
 __device__ long long r_search(const int4* __restrict__ epos, long long* __restrict__ ed, int n, int4 pc,
                               const PredConst& c, SelShared& S, const int small_n, const int cap, const int nb) {
@@ -291,12 +310,13 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
     if (tid == 0 && first_pass) S.dmax_all = 0;
     __syncthreads();
     unsigned long long span = whi - wlo + 1;  // mode 1 only
+    unsigned long long dmax = 0;              // this thread's farthest member (first pass)
     for (int j = tid; j < n; j += blockDim.x) {
       unsigned long long d;
       if (first_pass) {
         d = (unsigned long long)dist2(pc, epos[j]);
         ed[j] = (long long)d;
-        atomicMax(&S.dmax_all, d);
+        dmax = d > dmax ? d : dmax;
       } else {
         d = (unsigned long long)ed[j];
       }
@@ -308,8 +328,12 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
         b = (int)(((d - wlo) * (unsigned long long)nb) / span);
       }
       atomicAdd(&S.cnt[b], 1u);
-      atomicMin(&S.dmn[b], d);
-      atomicMax(&S.dmx[b], d);
+      bin_minmax(S, b, d);
+    }
+    if (first_pass) {
+      // one shared atomic per warp (per member it serialised on one address)
+      const unsigned long long m = warp_max_u64(dmax);
+      if ((tid & 31) == 0) atomicMax(&S.dmax_all, m);
     }
     __syncthreads();
     first_pass = false;
@@ -729,12 +753,13 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
       if (tid == 0 && first) S.dmax_all = 0;
       __syncthreads();
       const unsigned long long span = whi - wlo + 1;
+      unsigned long long dmax = 0;  // this thread's farthest member (first pass)
       for (int j = lo_r + tid; j < hi_r; j += blockDim.x) {
         unsigned long long d;
         if (first) {
           d = (unsigned long long)dist2(pc, epos[j]);
           ed[j] = (long long)d;
-          atomicMax(&S.dmax_all, d);
+          dmax = d > dmax ? d : dmax;
         } else {
           d = (unsigned long long)ed[j];
         }
@@ -746,8 +771,11 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
           b = (int)(((d - wlo) * (unsigned long long)nb) / span);
         }
         atomicAdd(&S.cnt[b], 1u);
-        atomicMin(&S.dmn[b], d);
-        atomicMax(&S.dmx[b], d);
+        bin_minmax(S, b, d);
+      }
+      if (first) {
+        const unsigned long long m = warp_max_u64(dmax);
+        if ((tid & 31) == 0) atomicMax(&S.dmax_all, m);
       }
       __syncthreads();
       cluster.sync();  // every CTA's histogram of its members is complete

@@ -243,53 +243,74 @@ __device__ __forceinline__ double wrap_box(double c) {
   return c;
 }
 
-__device__ __forceinline__ long long block_sum_ll(long long v, long long* sh) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  long long t = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-  __syncthreads();
-  return t;
-}
-
 // Statistics of every L1 halo over its members (the L2-level segments).
-// Pass one, one thread per member: the minimum-image offsets of the member
-// from its halo's nucleus, and from the halo's first L2 nucleus for members
-// of that L2 halo, summed exactly per halo in int64 (lanes of a warp that
-// share a halo add once); pass two, one thread per halo, forms the row.
-__global__ void k_summary_sums(const uint32_t* __restrict__ ehal2, int na, const int4* __restrict__ epos2,
-                               const int* __restrict__ ehalo2, const uint32_t* __restrict__ hnuc,
-                               const int4* __restrict__ epos, const uint32_t* __restrict__ nnuc2,
-                               const uint32_t* __restrict__ hbase2, const uint32_t* __restrict__ hnuc2,
-                               unsigned long long* __restrict__ acc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool v = i < na;
-  const int h = v ? (int)ehal2[i] : -1;
-  long long s[6] = {0, 0, 0, 0, 0, 0};
-  if (v) {
-    const int4 q = epos2[i];
-    const int4 pn = epos[hnuc[h]];
-    s[0] = mi(q.x - pn.x);
-    s[1] = mi(q.y - pn.y);
-    s[2] = mi(q.z - pn.z);
-    if (nnuc2[h] > 0 && ehalo2[i] == (int)hbase2[h]) {
-      const int4 p2 = epos2[hnuc2[hbase2[h]]];
-      s[3] = mi(q.x - p2.x);
-      s[4] = mi(q.y - p2.y);
-      s[5] = mi(q.z - p2.z);
+// Pass one (k_summary_sums): the minimum-image offsets of every member from
+// its halo's nucleus, and from the halo's first L2 nucleus for members of
+// that L2 halo, summed exactly per halo in int64; pass two, one thread per
+// halo, forms the row.
+// Per-halo sums of the members' minimum-image offsets from the L1 nucleus
+// (and, for members of the halo's first L2 subhalo, from that nucleus).  The
+// members come sorted by halo; a warp takes 32 x SUM_ITEMS consecutive ones,
+// sums each halo's lanes with one warp reduction per component, carries the
+// halo that runs on across items in registers, and adds a halo's partial sums
+// to acc once per warp (per-warp atomics on the accumulators of the biggest
+// halos serialised).  One offset is below 2^20 in magnitude, so 32 of them
+// sum exactly in 32 bits.
+constexpr int SUM_ITEMS = 16;
+__global__ void __launch_bounds__(256) k_summary_sums(const uint32_t* __restrict__ ehal2, int na,
+                                                      const int4* __restrict__ epos2, const int* __restrict__ ehalo2,
+                                                      const uint32_t* __restrict__ hnuc, const int4* __restrict__ epos,
+                                                      const uint32_t* __restrict__ nnuc2,
+                                                      const uint32_t* __restrict__ hbase2,
+                                                      const uint32_t* __restrict__ hnuc2,
+                                                      unsigned long long* __restrict__ acc) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 * SUM_ITEMS;
+  int open_h = -1;  // the halo carried over from earlier items
+  long long run[6] = {0, 0, 0, 0, 0, 0};
+  for (int it = 0; it < SUM_ITEMS; ++it) {
+    const long long i = w0 + (long long)it * 32 + lane;
+    const bool v = i < na;
+    const int h = v ? (int)ehal2[i] : -1;
+    int s[6] = {0, 0, 0, 0, 0, 0};
+    if (v) {
+      const int4 q = epos2[i];
+      const int4 pn = epos[hnuc[h]];
+      s[0] = mi(q.x - pn.x);
+      s[1] = mi(q.y - pn.y);
+      s[2] = mi(q.z - pn.z);
+      if (nnuc2[h] > 0 && ehalo2[i] == (int)hbase2[h]) {
+        const int4 p2 = epos2[hnuc2[hbase2[h]]];
+        s[3] = mi(q.x - p2.x);
+        s[4] = mi(q.y - p2.y);
+        s[5] = mi(q.z - p2.z);
+      }
     }
-  }
-  const unsigned peers = __match_any_sync(0xffffffffu, h);
-  const int leader = __ffs(peers) - 1;
+    const unsigned peers = __match_any_sync(0xffffffffu, h);
+    const bool lead = lane == __ffs(peers) - 1;
+    const int last_h = __shfl_sync(0xffffffffu, h, 31);
+    const unsigned omask = __ballot_sync(0xffffffffu, h == open_h && open_h >= 0);
+    const int olane = omask ? __ffs(omask) - 1 : 0;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    long long t = 0;
-    for (unsigned m = peers; m; m &= m - 1) t += __shfl_sync(peers, s[k], __ffs(m) - 1);
-    if (v && (int)(threadIdx.x & 31) == leader && t) atomicAdd(&acc[6 * (size_t)h + k], (unsigned long long)t);
+    for (int k = 0; k < 6; ++k) {
+      const int t = __reduce_add_sync(peers, s[k]);
+      const long long t_open = (long long)__shfl_sync(0xffffffffu, t, olane);
+      const long long t_last = (long long)__shfl_sync(0xffffffffu, t, 31);
+      // a halo wholly inside this item: its leader adds it
+      if (v && lead && h != open_h && h != last_h && t)
+        atomicAdd(&acc[6 * (size_t)h + k], (unsigned long long)(long long)t);
+      if (omask) run[k] += t_open;
+      if (last_h != open_h) {
+        // the carried halo ended: flush it and carry the last lane's halo
+        if (lane == 0 && open_h >= 0 && run[k]) atomicAdd(&acc[6 * (size_t)open_h + k], (unsigned long long)run[k]);
+        run[k] = t_last;
+      }
+    }
+    open_h = last_h;
   }
+  if (lane == 0 && open_h >= 0)
+    for (int k = 0; k < 6; ++k)
+      if (run[k]) atomicAdd(&acc[6 * (size_t)open_h + k], (unsigned long long)run[k]);
 }
 
 __global__ void k_summary(const uint32_t* __restrict__ seg2, int H1, const int4* __restrict__ epos2,
@@ -678,7 +699,8 @@ int run_groups(cso_ctx* c, const cso_params* p, const GroupsIn& gi, Stages& S, M
       ALLOC(unsigned long long, acc, 6 * (size_t)H1);
       CSO_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 6 * (size_t)H1, st));
       if (na > 0)
-        k_summary_sums<<<G1(na)>>>(ehal2, na, epos2, ehalo2, hnuc, epos, nnuc2, hbase2, hnuc2, acc);
+        k_summary_sums<<<CL(cdiv(na, 256 * SUM_ITEMS)), 256, 0, st>>>(ehal2, na, epos2, ehalo2, hnuc, epos, nnuc2,
+                                                                      hbase2, hnuc2, acc);
       k_summary<<<G1(H1)>>>(seg2, H1, epos2, hnuc, hR2, epos, eid, gs, root, minid, nnuc2, hbase2, hnuc2, h2size,
                             acc, ek2, 1.0 / p->l_mean_grid, p->np_min_L1, gi.x0, rows, keep);
     }

@@ -16,10 +16,11 @@
 
 #include "cells.cuh"
 
-// 64 MiB: 2^20 particles x 40 B (cell key, in-cell rank, sorted int4
-// position, sorted kernel sum, sorted id slot) plus a table of up to
-// 4,194,304 + 1 cell offsets and the scan's tile sums
-#define CSO_STATIC_SCRATCH_BYTES (64u << 20)
+// 80 MiB: 2^20 particles x 64 B (sorted int4 position, sorted kernel sum,
+// sorted id slot, and the binning's 16-byte placement record; the cell keys
+// and arrival ranks share the position array) plus a table of up to
+// 4,194,304 + 1 cell offsets and the scan's status words
+#define CSO_STATIC_SCRATCH_BYTES (80u << 20)
 
 static __device__ __align__(256) unsigned char g_cso_static_scratch[CSO_STATIC_SCRATCH_BYTES];
 
