@@ -433,24 +433,29 @@ __device__ long long r_search(const int4* __restrict__ epos, long long* __restri
 
 // Step 2's density criterion for cell-sorted particle se of group glabel: no
 // particle of the same group within d < b2 comes before it in key order
-// (Sigma desc, id asc).  One warp scans the 27-cell stencil, its own cell row
-// first (where a denser neighbour usually sits), and stops at the first beater.
-__device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
+// (Sigma desc, id asc).  The neighbours are the runs of the 27-cell stencil,
+// nine rows (own row first, where a denser neighbour usually sits), each one
+// run plus one where the row wraps; rows and end cells that cannot reach
+// within b are dropped.
+struct PeakRows {
+  uint32_t lo0, hi0, lo1, hi1;  // lanes 0-8: row lane's runs (rows in walk order)
+  int qx1, qy, qz;              // the query in that row's image
+  uint32_t pre;                 // lanes 0-9: neighbours in the rows before this one
+};
+
+__device__ __forceinline__ int peak_row_of(int o) { return o == 0 ? 4 : (o <= 4 ? o - 1 : o); }
+
+__device__ PeakRows peak_rows(const LevelArgs& a, int4 p) {
   const int lane = threadIdx.x & 31;
-  const int4 p = a.spos[se];
-  const long long sp = a.ssig[se];
-  const uint64_t idp = a.sid[se];
   const CellGrid& g = a.grid;
   const int nc = g.nc;
   const int cy = cell_coord(p.y, nc), cz = cell_coord(p.z, nc);
   const int tc = grid_col(g, p.x);
   const XCells X = x_cells(g, tc);
-  // lane r < 9 looks up row r = (dz + 1) * 3 + (dy + 1), dropping the rows and
-  // end cells that cannot reach within b (one run, plus one where the row wraps)
-  uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-  int qx1 = p.x, qy = p.y, qz = p.z;
+  PeakRows R{0, 0, 0, 0, p.x, p.y, p.z, 0};
   if (lane < 9) {
-    const int dz = lane / 3 - 1, dy = lane % 3 - 1;
+    const int r = peak_row_of(lane);
+    const int dz = r / 3 - 1, dy = r % 3 - 1;
     const int gx = (p.x + g.x0) & (CSO_BOX - 1), gcx = cell_coord(gx, nc);
     const long long zl = p.z - cell_lo(cz, nc) + 1, zr = cell_lo(cz + 1, nc) - p.z;
     const long long yl = p.y - cell_lo(cy, nc) + 1, yr = cell_lo(cy + 1, nc) - p.y;
@@ -459,57 +464,110 @@ __device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
     if (m < (long long)a.b2) {
       int sz, sy;
       const int zz = wrap_yz(cz + dz, nc, sz), yy = wrap_yz(cy + dy, nc, sy);
-      qz += sz;
-      qy += sy;
+      R.qz += sz;
+      R.qy += sy;
       const uint32_t* row = grid_row(g, zz, yy);
       const bool left = m + xl * xl < (long long)a.b2, right = m + xr * xr < (long long)a.b2;
       const int ca = left ? X.a : tc, cb = right ? X.b : tc;
-      if (left && X.wl >= 0) { lo1 = row[X.wl]; hi1 = row[X.wl + 1]; qx1 = p.x + CSO_BOX; }
-      if (right && X.wr >= 0) { lo1 = row[X.wr]; hi1 = row[X.wr + 1]; qx1 = p.x - CSO_BOX; }
-      lo0 = row[ca];
-      hi0 = row[cb + 1];
+      if (left && X.wl >= 0) { R.lo1 = row[X.wl]; R.hi1 = row[X.wl + 1]; R.qx1 = p.x + CSO_BOX; }
+      if (right && X.wr >= 0) { R.lo1 = row[X.wr]; R.hi1 = row[X.wr + 1]; R.qx1 = p.x - CSO_BOX; }
+      R.lo0 = row[ca];
+      R.hi0 = row[cb + 1];
     }
   }
-  for (int o = 0; o < 9; ++o) {
-    const int r = o == 0 ? 4 : (o <= 4 ? o - 1 : o);  // own row first
-    const uint32_t l0 = __shfl_sync(0xffffffffu, lo0, r), h0 = __shfl_sync(0xffffffffu, hi0, r);
-    const uint32_t l1 = __shfl_sync(0xffffffffu, lo1, r), h1 = __shfl_sync(0xffffffffu, hi1, r);
-    const int x1 = __shfl_sync(0xffffffffu, qx1, r), y = __shfl_sync(0xffffffffu, qy, r);
-    const int z = __shfl_sync(0xffffffffu, qz, r);
-    const uint32_t n0 = h0 - l0, tot = n0 + (h1 - l1);
-    // four neighbours per lane per step: every load of the step is issued
-    // before any comparison, so a step costs one memory round trip, not four
-    constexpr int U = 4;
-    for (uint32_t f0 = 0; f0 < tot; f0 += 32 * U) {
-      int4 q[U];
-      int lab[U];
-      long long st[U];
-      uint32_t tt[U];
+  // exclusive prefix of the rows' neighbour counts (lane 9 holds the total)
+  const uint32_t cnt = lane < 9 ? (R.hi0 - R.lo0) + (R.hi1 - R.lo1) : 0u;
+  uint32_t inc = cnt;
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const uint32_t f = f0 + k * 32 + lane;
-        tt[k] = f < tot ? (f < n0 ? l0 + f : l1 + (f - n0)) : se;
-        q[k] = a.spos[tt[k]];
-        lab[k] = a.slab[tt[k]];
-        st[k] = a.ssig[tt[k]];
-      }
-      bool beat = false;
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const uint32_t f = f0 + k * 32 + lane;
-        if (tt[k] == se || lab[k] != glabel) continue;  // past the end (tt = se), self, or another group
-        const int qx = f < n0 ? p.x : x1;
-        const int dx = qx - q[k].x, dy = y - q[k].y, dz = z - q[k].z;
-        const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
-        if (d < a.b2) beat = beat || st[k] > sp || (st[k] == sp && a.sid[tt[k]] < idp);
-      }
-      if (__any_sync(0xffffffffu, beat)) return false;
-    }
+  for (int o = 1; o < 16; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
   }
-  return true;
+  R.pre = inc - cnt;
+  return R;
 }
 
-// One group (segment) of a level, processed by a block of NT threads.
+// One load step of the peak test: neighbours f0 + k * 32 + lane (k < U) of
+// the flattened rows; true if any lane found a beater.  Every load of the
+// step is issued before any comparison, so a step costs one memory round trip.
+constexpr int PEAK_U = 4;
+__device__ __forceinline__ bool peak_step(const LevelArgs& a, const PeakRows& R, uint32_t f0, uint32_t total, uint32_t se,
+                                          int glabel, int4 p, long long sp, uint64_t idp) {
+  const int lane = threadIdx.x & 31;
+  int4 q[PEAK_U];
+  int lab[PEAK_U];
+  long long st[PEAK_U];
+  uint32_t tt[PEAK_U];
+  int ow[PEAK_U];  // row (walk order) | 16 for the wrapped run
+#pragma unroll
+  for (int k = 0; k < PEAK_U; ++k) {
+    const uint32_t f = f0 + k * 32 + lane;
+    // the row holding f: the last o with pre[o] <= f
+    int o = 0;
+#pragma unroll
+    for (int oo = 1; oo < 9; ++oo)
+      if (__shfl_sync(0xffffffffu, R.pre, oo) <= f) o = oo;
+    const uint32_t r = f - __shfl_sync(0xffffffffu, R.pre, o);
+    const uint32_t l0 = __shfl_sync(0xffffffffu, R.lo0, o), n0 = __shfl_sync(0xffffffffu, R.hi0, o) - l0;
+    const uint32_t l1 = __shfl_sync(0xffffffffu, R.lo1, o);
+    tt[k] = f < total ? (r < n0 ? l0 + r : l1 + (r - n0)) : se;
+    ow[k] = o | (r < n0 ? 0 : 16);
+    q[k] = a.spos[tt[k]];
+    lab[k] = a.slab[tt[k]];
+    st[k] = a.ssig[tt[k]];
+  }
+  bool beat = false;
+#pragma unroll
+  for (int k = 0; k < PEAK_U; ++k) {
+    const int o = ow[k] & 15;
+    const int x1 = __shfl_sync(0xffffffffu, R.qx1, o), yq = __shfl_sync(0xffffffffu, R.qy, o),
+              zq = __shfl_sync(0xffffffffu, R.qz, o);
+    if (tt[k] == se || lab[k] != glabel) continue;  // past the end (tt = se), self, or another group
+    const int dx = (ow[k] & 16 ? x1 : p.x) - q[k].x, dy = yq - q[k].y, dz = zq - q[k].z;
+    const uint32_t d = (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+    if (d < a.b2) beat = beat || st[k] > sp || (st[k] == sp && a.sid[tt[k]] < idp);
+  }
+  return __any_sync(0xffffffffu, beat);
+}
+
+enum : int { PEAK_NO = 0, PEAK_YES = 1, PEAK_OPEN = 2 };
+
+// The test by one warp, at most `steps` load steps: PEAK_NO (a beater was
+// found), PEAK_YES (no beater among all neighbours) or PEAK_OPEN (not
+// finished; peak_part finishes it with many warps).
+__device__ __forceinline__ int warp_peak(const LevelArgs& a, uint32_t se, int glabel, int steps) {
+  const int4 p = a.spos[se];
+  const long long sp = a.ssig[se];
+  const uint64_t idp = a.sid[se];
+  const PeakRows R = peak_rows(a, p);
+  const uint32_t total = __shfl_sync(0xffffffffu, R.pre, 9);
+  for (uint32_t f0 = 0; f0 < total; f0 += 32 * PEAK_U) {
+    if (steps-- <= 0) return PEAK_OPEN;
+    if (peak_step(a, R, f0, total, se, glabel, p, sp, idp)) return PEAK_NO;
+  }
+  return PEAK_YES;
+}
+
+// Part `part` of `parts` of the test (warps of a block or of a cluster
+// share the neighbours step by step): true if this part holds a beater.
+__device__ __forceinline__ bool peak_part_beaten(const LevelArgs& a, uint32_t se, int glabel, int part, int parts) {
+  const int4 p = a.spos[se];
+  const long long sp = a.ssig[se];
+  const uint64_t idp = a.sid[se];
+  const PeakRows R = peak_rows(a, p);
+  const uint32_t total = __shfl_sync(0xffffffffu, R.pre, 9);
+  for (uint32_t f0 = (uint32_t)part * 32 * PEAK_U; f0 < total; f0 += (uint32_t)parts * 32 * PEAK_U)
+    if (peak_step(a, R, f0, total, se, glabel, p, sp, idp)) return true;
+  return false;
+}
+
+// load steps a warp spends on a candidate before the test goes to all warps
+constexpr int PEAK_STEPS = 4;
+
+__device__ bool warp_is_peak(const LevelArgs& a, uint32_t se, int glabel) {
+  return warp_peak(a, se, glabel, INT_MAX) == PEAK_YES;
+}
+
 template <int NT>
 __device__ void level_block(const LevelArgs& a, const int seg) {
   constexpr int NW = NT / 32;
@@ -517,6 +575,7 @@ __device__ void level_block(const LevelArgs& a, const int seg) {
   __shared__ int sP;
   __shared__ int list[NT];
   __shared__ int peak_of[NW];
+  __shared__ int coop_beat;
   const unsigned base = a.seg_off[seg];
   const int n = (int)(a.seg_off[seg + 1] - base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -556,19 +615,30 @@ __device__ void level_block(const LevelArgs& a, const int seg) {
     if (f) list[excl] = j;
     __syncthreads();
     for (int g0 = 0; g0 < (int)m; g0 += NW) {
-      // step 2 for up to NW of them at once, one warp each (peak-ness never changes)
+      // step 2 for up to NW of them at once, one warp each for at most
+      // PEAK_STEPS load steps (peak-ness never changes)
       const int k = g0 + warp;
       if (k < (int)m) {
         const int e = list[k];
-        const bool ok = !einel[e] && warp_is_peak(a, egs[e], glabel);
-        if (lane == 0) peak_of[warp] = ok;
+        const int st = einel[e] ? PEAK_NO : warp_peak(a, egs[e], glabel, PEAK_STEPS);
+        if (lane == 0) peak_of[warp] = st;
       }
       __syncthreads();
       const int kmax = min(NW, (int)m - g0);
       for (int kk = 0; kk < kmax; ++kk) {
         const int e = list[g0 + kk];
         // eligibility may have been lost to a nucleus found earlier in this walk
-        if (!peak_of[kk] || einel[e]) continue;
+        if (peak_of[kk] == PEAK_NO || einel[e]) continue;
+        if (peak_of[kk] == PEAK_OPEN) {
+          // a test one warp did not finish: every warp of the block takes a share
+          if (tid == 0) coop_beat = 0;
+          __syncthreads();
+          if (peak_part_beaten(a, egs[e], glabel, warp, NW) && lane == 0) coop_beat = 1;
+          __syncthreads();
+          const bool beaten = coop_beat != 0;
+          __syncthreads();
+          if (beaten) continue;
+        }
         const int4 pc = epos[e];
         const long long R2 = r_search<NT>(epos, ed, n, pc, a.pc, S, a.small_n, a.cap, a.nb);
         // steps 1 and 3
@@ -640,6 +710,8 @@ struct ClusterCtl {
   int bin;                  // bin being gathered
   unsigned in_window;
   int blo, bn, bend;        // candidate batch of the nucleus walk
+  int coop;                 // batch entry whose peak test every warp shares, or -1
+  int cbeat;                // that test found a beater
 };
 
 struct ClusterGen {  // the leader's resumable walk over eligible candidates
@@ -874,6 +946,75 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
   return R2;
 }
 
+// Step 2 walk of the cluster tier: the next candidate in key order that is
+// eligible and a local peak (member index), or -1.  The leader hands out
+// batches; every warp of every CTA peak-tests one candidate for at most
+// PEAK_STEPS load steps and stores the state in the leader's shared memory;
+// the leader's thread 0 takes the first candidate of the batch still in
+// play, and a test no warp finished is finished by every warp of the cluster
+// before it is decided (no nucleus is accepted during the walk, so a batch
+// is settled in order).  Every CTA passes the same barriers: the exits are
+// read from the leader after a barrier.
+__device__ __forceinline__ int cluster_walk(const LevelArgs& a, const uint32_t* __restrict__ egs,
+                                         const uint8_t* __restrict__ einel, int glabel, SelShared& S,
+                                         ClusterCtl& C, ClusterGen& G) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const bool leader = rank == 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  ClusterCtl* LC = cluster.map_shared_rank(&C, 0);
+  ClusterGen* LG = cluster.map_shared_rank(&G, 0);
+  int e = -1;
+  while (true) {
+    if (leader) leader_next_batch(einel, C.P, G, C, S);
+    cluster.sync();  // batch published
+    if (LC->bend) break;
+    const int blo = LC->blo, bn = LC->bn;
+    const int k = blo + rank * 32 + warp;
+    if (k < blo + bn) {
+      const int ek = LG->list[k];
+      const int st = einel[ek] ? PEAK_NO : warp_peak(a, egs[ek], glabel, PEAK_STEPS);
+      if (lane == 0) LG->peak_of[k] = (int8_t)st;
+    }
+    cluster.sync();  // peak states in the leader's shared memory
+    int from = blo;
+    while (true) {
+      // the leader takes the first candidate of the batch still in play: a
+      // settled peak is the nucleus; an open test goes to every warp of
+      // the cluster first
+      if (leader && tid == 0) {
+        int kk = from, found = -1, coop = -1;
+        for (const int kend = C.blo + C.bn; kk < kend; ++kk) {
+          const int ec = G.list[kk];
+          if (G.peak_of[kk] == PEAK_NO || einel[ec]) continue;
+          if (G.peak_of[kk] == PEAK_OPEN) {
+            coop = kk;
+            break;
+          }
+          found = ec;
+          ++kk;
+          break;
+        }
+        G.pos = kk;
+        C.e = found;
+        C.coop = coop;
+        C.cbeat = 0;
+      }
+      cluster.sync();  // walk decision (or the shared test) published
+      const int kc = LC->coop;
+      if (kc < 0) break;
+      if (peak_part_beaten(a, egs[LG->list[kc]], glabel, rank * 32 + warp, CL_CS * 32) && lane == 0)
+        atomicExch(&LC->cbeat, 1);
+      cluster.sync();  // every share of the shared test done
+      if (leader && tid == 0) G.peak_of[kc] = (int8_t)(C.cbeat ? PEAK_NO : PEAK_YES);
+      from = kc;
+    }
+    e = LC->e;
+    if (e >= 0) break;
+  }
+  return e;
+}
+
 __device__ void cluster_level(const LevelArgs& a, const int seg, SelShared& S, ClusterCtl& C, ClusterGen& G) {
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -914,43 +1055,7 @@ __device__ void cluster_level(const LevelArgs& a, const int seg, SelShared& S, C
   cluster.sync();  // slots and flags initialised everywhere
   int nn = 0;
   while (true) {
-    // Step 2 walk: the next candidate in key order that is eligible and a
-    // local peak.  The leader hands out batches; every warp of every CTA
-    // peak-tests one candidate and stores the flag in the leader's shared
-    // memory; the leader's thread 0 takes the first candidate of the batch
-    // that passes (no nucleus is accepted during the walk, so the batch is
-    // settled at once).  Every CTA passes the same barriers: the exits are
-    // read from the leader after a barrier.
-    int e = -1;
-    while (true) {
-      if (leader) leader_next_batch(einel, C.P, G, C, S);
-      cluster.sync();  // batch published
-      if (LC->bend) break;
-      const int blo = LC->blo, bn = LC->bn;
-      const int k = blo + rank * 32 + warp;
-      if (k < blo + bn) {
-        const int ek = LG->list[k];
-        const bool ok = !einel[ek] && warp_is_peak(a, egs[ek], glabel);
-        if (lane == 0) LG->peak_of[k] = (int8_t)ok;
-      }
-      cluster.sync();  // peak flags in the leader's shared memory
-      if (leader && tid == 0) {
-        int kk = C.blo, found = -1;
-        for (const int kend = C.blo + C.bn; kk < kend; ++kk) {
-          const int ec = G.list[kk];
-          if (G.peak_of[kk] && !einel[ec]) {
-            found = ec;
-            ++kk;
-            break;
-          }
-        }
-        G.pos = kk;
-        C.e = found;
-      }
-      cluster.sync();  // walk decision published
-      e = LC->e;
-      if (e >= 0) break;
-    }
+    const int e = cluster_walk(a, egs, einel, glabel, S, C, G);
     if (e < 0) break;
     const int4 pc = epos[e];
     const long long R2 = cluster_r_search(cluster, epos, ed, n, lo_r, hi_r, pc, a.pc, S, C, a.cap, a.nb);
