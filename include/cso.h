@@ -332,7 +332,7 @@ int cso_struct_sizes(int64_t* out, int n);
  * [n][3]) and sigma (int64 [n], input order) are DEVICE pointers owned by
  * the caller; stream is a cudaStream_t (NULL = legacy default stream); the
  * call returns after the work on that stream has completed.  The scratch
- * lives in one fixed 80 MiB array in device memory that every GPU which
+ * lives in one fixed 96 MiB array in device memory that every GPU which
  * loads this library holds until the process exits; nothing is allocated or
  * freed.  Limits: n <= CSO_STATIC_MAX_N and at most CSO_STATIC_MAX_CELLS
  * cells (boxes of up to 64 l_mean per side at the default b); larger requests

@@ -82,19 +82,22 @@ __global__ void k_cell_count(const int32_t* __restrict__ pos, long long n, CellG
   rank[i] = atomicAdd(&count[k], 1u);
 }
 
-// What k_cell_place needs of the particle at a provisional slot: its sort
-// key (stored x << 32 | input index) and its cell's range, so that the
-// placement reads neither the positions' cells nor the table again.
-struct __align__(16) BinRec {
+// Everything k_cell_place needs of the particle at a provisional slot: its
+// sort key (stored x << 32 | input index), its cell's range, its stored y and
+// z and its id.  One record is one 32-byte sector, so the scatter writes
+// whole sectors and the placement reads nothing from scattered places.
+struct __align__(32) BinRec {
   unsigned long long key;
   uint32_t c0, m;
+  int y, z;
+  unsigned long long id;
 };
 
-// Provisional slot of every particle (cell start + arrival rank): only the
-// 16-byte record is scattered (one sector either way), and inv (optional)
-// receives the provisional slot in input order.
-__global__ void k_cell_scatter(const int32_t* __restrict__ pos, long long n, CellGrid g,
-                               const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+// Provisional slot of every particle (cell start + arrival rank): the record
+// is scattered there, and inv (optional) receives the provisional slot in
+// input order.
+__global__ void k_cell_scatter(const int32_t* __restrict__ pos, const uint64_t* __restrict__ ids, long long n,
+                               CellGrid g, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
                                const uint32_t* __restrict__ start, BinRec* __restrict__ rec,
                                uint32_t* __restrict__ inv) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -102,11 +105,13 @@ __global__ void k_cell_scatter(const int32_t* __restrict__ pos, long long n, Cel
   const int4 q = stored_pos(pos, (size_t)i, g);
   const uint32_t k = key[i], c0 = start[k], c1 = start[k + 1];
   const uint32_t p = c0 + rank[i];
-  BinRec r;
-  r.key = ((unsigned long long)(unsigned)q.x << 32) | (unsigned long long)i;
-  r.c0 = c0;
-  r.m = c1 - c0;
-  rec[p] = r;
+  // one 256-bit store: the whole sector in one scattered write
+  const unsigned long long w0 = ((unsigned long long)(unsigned)q.x << 32) | (unsigned long long)i;
+  const unsigned long long w1 = (unsigned long long)c0 | ((unsigned long long)(c1 - c0) << 32);
+  const unsigned long long w2 = (unsigned long long)(unsigned)q.y | ((unsigned long long)(unsigned)q.z << 32);
+  const unsigned long long w3 = ids[i];
+  asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(rec + p), "l"(w0), "l"(w1), "l"(w2), "l"(w3)
+               : "memory");
   if (inv) inv[i] = p;
 }
 
@@ -115,25 +120,29 @@ __global__ void k_cell_scatter(const int32_t* __restrict__ pos, long long n, Cel
 // (y, z) row of adjacent x cells, is sorted by x (the density pass bounds its
 // runs by x).  A lane counts a cell of up to 32 particles alone; the warp
 // streams each larger cell once through shared memory for all its lanes in
-// that cell.  The positions and ids are read from their scattered input
-// places and written into the cell's range; fin (optional) maps the
-// provisional slot to the final one (k_cell_inv composes it into inv).
+// that cell.  Position and id come with the record and are written into the
+// cell's range; fin (optional) maps the provisional slot to the final one
+// (k_cell_inv composes it into inv).
 constexpr int PLACE_SMALL = 32;
-__global__ void __launch_bounds__(256) k_cell_place(const int32_t* __restrict__ pos,
-                                                    const uint64_t* __restrict__ ids, long long n, CellGrid g,
-                                                    const BinRec* __restrict__ rec, int4* __restrict__ spos,
-                                                    uint64_t* __restrict__ sid, uint32_t* __restrict__ fin) {
+__global__ void __launch_bounds__(256) k_cell_place(long long n, const BinRec* __restrict__ rec,
+                                                    int4* __restrict__ spos, uint64_t* __restrict__ sid,
+                                                    uint32_t* __restrict__ fin) {
   __shared__ unsigned long long tile[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = t < n;
-  unsigned long long kt = 0;
+  unsigned long long kt = 0, id = 0;
   uint32_t c0 = 0, c1 = 0;
+  int y = 0, z = 0;
   if (act) {
-    const BinRec r = rec[t];
-    kt = r.key;
-    c0 = r.c0;
-    c1 = r.c0 + r.m;
+    unsigned long long w0, w1, w2, w3;
+    asm volatile("ld.global.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3) : "l"(rec + t));
+    kt = w0;
+    c0 = (uint32_t)w1;
+    c1 = c0 + (uint32_t)(w1 >> 32);
+    y = (int)(uint32_t)w2;
+    z = (int)(uint32_t)(w2 >> 32);
+    id = w3;
   }
   const bool big = act && c1 - c0 > (uint32_t)PLACE_SMALL;
   uint32_t rk = 0;
@@ -156,10 +165,9 @@ __global__ void __launch_bounds__(256) k_cell_place(const int32_t* __restrict__ 
     pend &= ~__ballot_sync(0xffffffffu, mine);
   }
   if (!act) return;
-  const uint32_t i = (uint32_t)kt;
   const uint32_t d = c0 + rk;
-  spos[d] = stored_pos(pos, i, g);
-  sid[d] = ids[i];
+  spos[d] = make_int4((int)(kt >> 32), y, z, (int)(uint32_t)kt);
+  sid[d] = id;
   if (fin) fin[t] = d;
 }
 
@@ -1020,8 +1028,8 @@ int cells_bin(const int32_t* pos, const uint64_t* ids, long long n, const CellGr
   if (n > 0) {
     CellGrid gs = g;
     gs.start = start;
-    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, n, gs, key, rank, start, rec, inv);
-    k_cell_place<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, gs, rec, spos, sid, fin);
+    k_cell_scatter<<<CL(cdiv(n, 256)), 256, 0, st>>>(pos, ids, n, gs, key, rank, start, rec, inv);
+    k_cell_place<<<CL(cdiv(n, 256)), 256, 0, st>>>(n, rec, spos, sid, fin);
     if (inv) k_cell_inv<<<CL(cdiv(n, 256)), 256, 0, st>>>(n, fin, inv);
     CSO_CUDA(cudaGetLastError());
   }

@@ -54,7 +54,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* smem_w
 constexpr int SP_THREADS = 256;
 // values per thread: 16 (tiles of 4,096), or 32 for arrays of more than
 // SP_BIG values (half the tiles and look-backs, twice the loads in flight)
-constexpr long long SP_BIG = 1ll << 25;
+constexpr long long SP_BIG = 1ll << 22;
 constexpr unsigned long long SP_A = 1ull << 32, SP_P = 2ull << 32;
 constexpr long long SP_SPIN_LIMIT = 1ll << 22;
 
@@ -73,31 +73,46 @@ __global__ void __launch_bounds__(SP_THREADS) k_scan_onepass(uint32_t* __restric
                                                              unsigned long long* __restrict__ status, long long ntiles,
                                                              uint32_t* __restrict__ total, int* __restrict__ err) {
   constexpr int SP_TILE = SP_THREADS * SP_ITEMS;
+  constexpr int R = SP_ITEMS / 4;  // rounds of four consecutive values per lane
   __shared__ uint32_t sw[33];
   __shared__ long long tile_sh;
   __shared__ uint32_t prefix_sh;
   if (threadIdx.x == 0) tile_sh = (long long)atomicAdd(&status[ntiles], 1ull);
   __syncthreads();
   const long long tile = tile_sh;
-  const long long i0 = tile * SP_TILE + (long long)threadIdx.x * SP_ITEMS;
-  uint32_t v[SP_ITEMS];
-  if (i0 + SP_ITEMS <= n && ((reinterpret_cast<uintptr_t>(d + i0) & 15) == 0)) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // warp w holds a contiguous run of the tile; in round q its lanes hold 32
+  // consecutive groups of four values, so every load moves 512 contiguous bytes
+  const long long wb = tile * SP_TILE + (long long)w * 32 * SP_ITEMS;
+  const bool vec = wb + 32 * SP_ITEMS <= n && ((reinterpret_cast<uintptr_t>(d) & 15) == 0);
+  uint4 v[R];
 #pragma unroll
-    for (int q = 0; q < SP_ITEMS / 4; ++q) {
-      const uint4 w = reinterpret_cast<const uint4*>(d + i0)[q];
-      v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+  for (int q = 0; q < R; ++q) {
+    const long long i = wb + ((long long)q * 32 + lane) * 4;
+    if (vec) {
+      v[q] = *reinterpret_cast<const uint4*>(d + i);
+    } else {
+      v[q].x = i < n ? d[i] : 0u;
+      v[q].y = i + 1 < n ? d[i + 1] : 0u;
+      v[q].z = i + 2 < n ? d[i + 2] : 0u;
+      v[q].w = i + 3 < n ? d[i + 3] : 0u;
     }
-  } else {
-#pragma unroll
-    for (int k = 0; k < SP_ITEMS; ++k) v[k] = i0 + k < n ? d[i0 + k] : 0u;
   }
-  uint32_t s = 0;
+  // each round's exclusive prefix within the warp's run
+  uint32_t base[R];
+  uint32_t carry = 0;
 #pragma unroll
-  for (int k = 0; k < SP_ITEMS; ++k) s += v[k];
+  for (int q = 0; q < R; ++q) {
+    const uint32_t sq = v[q].x + v[q].y + v[q].z + v[q].w;
+    const uint32_t inc = warp_incl_scan(sq);
+    base[q] = carry + inc - sq;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  // the warps' runs in order: lane 0 carries its warp's total into the block scan
   uint32_t excl;
-  const uint32_t agg = block_excl_scan(s, sw, excl);
+  const uint32_t agg = block_excl_scan(lane == 0 ? carry : 0u, sw, excl);
+  const uint32_t woff = __shfl_sync(0xffffffffu, excl, 0);
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
     uint32_t prefix = 0;
     if (tile > 0) {
       if (lane == 0) sp_store(&status[tile], SP_A | agg);
@@ -105,8 +120,8 @@ __global__ void __launch_bounds__(SP_THREADS) k_scan_onepass(uint32_t* __restric
       long long spins = 0;
       for (;;) {
         const long long j = top - lane;
-        const unsigned long long w = j >= 0 ? sp_load(&status[j]) : SP_P;  // before tile 0: prefix 0
-        const unsigned long long flag = w & ~0xffffffffull;
+        const unsigned long long wv = j >= 0 ? sp_load(&status[j]) : SP_P;  // before tile 0: prefix 0
+        const unsigned long long flag = wv & ~0xffffffffull;
         const unsigned pmask = __ballot_sync(0xffffffffu, flag == SP_P);
         const unsigned xmask = __ballot_sync(0xffffffffu, flag == 0);
         const int firstP = pmask ? __ffs(pmask) - 1 : 31;
@@ -118,7 +133,7 @@ __global__ void __launch_bounds__(SP_THREADS) k_scan_onepass(uint32_t* __restric
           }
           continue;
         }
-        prefix += __reduce_add_sync(0xffffffffu, lane <= firstP ? (uint32_t)w : 0u);
+        prefix += __reduce_add_sync(0xffffffffu, lane <= firstP ? (uint32_t)wv : 0u);
         if (pmask) break;
         top -= 32;
       }
@@ -130,21 +145,19 @@ __global__ void __launch_bounds__(SP_THREADS) k_scan_onepass(uint32_t* __restric
     }
   }
   __syncthreads();
-  uint32_t run = prefix_sh + excl;
-  uint32_t o[SP_ITEMS];
+  const uint32_t off = prefix_sh + woff;
 #pragma unroll
-  for (int k = 0; k < SP_ITEMS; ++k) {
-    o[k] = run;
-    run += v[k];
-  }
-  if (i0 + SP_ITEMS <= n && ((reinterpret_cast<uintptr_t>(d + i0) & 15) == 0)) {
-#pragma unroll
-    for (int q = 0; q < SP_ITEMS / 4; ++q)
-      reinterpret_cast<uint4*>(d + i0)[q] = make_uint4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < SP_ITEMS; ++k)
-      if (i0 + k < n) d[i0 + k] = o[k];
+  for (int q = 0; q < R; ++q) {
+    const long long i = wb + ((long long)q * 32 + lane) * 4;
+    const uint32_t b0 = off + base[q], b1 = b0 + v[q].x, b2 = b1 + v[q].y, b3 = b2 + v[q].z;
+    if (vec) {
+      *reinterpret_cast<uint4*>(d + i) = make_uint4(b0, b1, b2, b3);
+    } else {
+      if (i < n) d[i] = b0;
+      if (i + 1 < n) d[i + 1] = b1;
+      if (i + 2 < n) d[i + 2] = b2;
+      if (i + 3 < n) d[i + 3] = b3;
+    }
   }
 }
 

@@ -16,11 +16,11 @@
 
 #include "cells.cuh"
 
-// 80 MiB: 2^20 particles x 64 B (sorted int4 position, sorted kernel sum,
-// sorted id slot, and the binning's 16-byte placement record; the cell keys
+// 96 MiB: 2^20 particles x 80 B (sorted int4 position, sorted kernel sum,
+// sorted id slot, and the binning's 32-byte placement record; the cell keys
 // and arrival ranks share the position array) plus a table of up to
 // 4,194,304 + 1 cell offsets and the scan's status words
-#define CSO_STATIC_SCRATCH_BYTES (80u << 20)
+#define CSO_STATIC_SCRATCH_BYTES (96u << 20)
 
 static __device__ __align__(256) unsigned char g_cso_static_scratch[CSO_STATIC_SCRATCH_BYTES];
 
