@@ -511,6 +511,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--bins", default="", help="giant,small size bins of the batched schedule instead of autotuning")
+    ap.add_argument("--huge", type=int, default=0, help="groups above this many members on 16-CTA clusters (0: library default)")
     ap.add_argument("--no-radial", action="store_true", help="skip timing the radial statistics stage")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -578,6 +579,8 @@ def main():
                 tuned = (g_, s_)
             else:  # size bins picked by the autotuner on this machine (untimed)
                 tuned = cso.cso_autotune(c.h, buf, params)
+            if args.huge:
+                cso.cso_set_huge_group(c.h, args.huge)
         stream = torch.cuda.ExternalStream(cso.cso_stream(c.h))
         for _ in range(args.warmup):
             cso.cso_find_groups(c.h, buf, params)

@@ -255,6 +255,14 @@ int cso_autotune(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_out
  * <= 64); the defaults are 16384 and 64. */
 int cso_set_schedule(cso_ctx* ctx, int32_t giant, int32_t small);
 
+/* Groups above max(huge, giant) members run on 16-CTA thread-block clusters
+ * (a non-portable cluster size) where the device can hold one, instead of
+ * 8-CTA clusters: the level passes of the few biggest groups are the batched
+ * schedule's critical path.  Default 524288 (2^19); huge >= 64, INT32_MAX
+ * keeps every group on 8-CTA clusters.  Outputs do not depend on it.
+ * Returns CSO_ERR_ARG for huge < 64. */
+int cso_set_huge_group(cso_ctx* ctx, int32_t huge);
+
 /* --- the three steps one at a time --------------------------------------
  *
  * For a caller that distributes one box over several GPUs (each GPU owns

@@ -326,6 +326,10 @@ def cso_set_schedule(ctx, giant, small):
     _check(lib().cso_set_schedule(ctx, int(giant), int(small)), "cso_set_schedule")
 
 
+def cso_set_huge_group(ctx, huge):
+    _check(lib().cso_set_huge_group(ctx, int(huge)), "cso_set_huge_group")
+
+
 def cso_submit(ctx, buffers, params):
     t = ctypes.c_uint64()
     rc = lib().cso_submit(ctx, ctypes.byref(buffers.cin), ctypes.byref(params), ctypes.byref(buffers.cout),

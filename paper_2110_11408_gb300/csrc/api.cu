@@ -149,6 +149,8 @@ extern "C" int cso_init(cso_ctx** out, int device, size_t budget, uint32_t flags
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join3, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, sizeof(long long) * 64);
   for (int i = 0; e == cudaSuccess && i <= CSO_MAX_STAGES; ++i) e = cudaEventCreate(&c->ev[i]);
   if (e != cudaSuccess) {
@@ -173,8 +175,11 @@ extern "C" void cso_free(cso_ctx* c) {
     if (c->graphs[i].exec) cudaGraphExecDestroy(c->graphs[i].exec);
   if (c->side) cudaStreamSynchronize(c->side);
   if (c->side2) cudaStreamSynchronize(c->side2);
+  if (c->side3) cudaStreamSynchronize(c->side3);
   if (c->join2) cudaEventDestroy(c->join2);
   if (c->side2) cudaStreamDestroy(c->side2);
+  if (c->join3) cudaEventDestroy(c->join3);
+  if (c->side3) cudaStreamDestroy(c->side3);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);
@@ -247,6 +252,15 @@ extern "C" int cso_set_schedule(cso_ctx* c, int32_t giant, int32_t small) {
   }
   c->sched.giant = giant;
   c->sched.small = small;
+  return CSO_OK;
+}
+
+extern "C" int cso_set_huge_group(cso_ctx* c, int32_t huge) {
+  if (!c || huge < 64) {
+    cso_set_error("the huge-group bound needs huge >= 64");
+    return CSO_ERR_ARG;
+  }
+  c->sched.huge = huge;
   return CSO_OK;
 }
 

@@ -693,7 +693,8 @@ __global__ void __launch_bounds__(NT) k_level(LevelArgs a, const uint32_t* __res
 // ---------------------------------------------------------------------------
 namespace cg = cooperative_groups;
 
-constexpr int CL_CS = 8;      // CTAs per cluster
+constexpr int CL_CS = 8;      // CTAs per cluster (giant groups)
+constexpr int CL_HUGE_CS = 16;  // CTAs per cluster for huge groups (non-portable size, where it fits)
 constexpr int CL_NT = 1024;   // threads per CTA
 
 enum : int { OP_DONE = 0, OP_HIST = 1, OP_GATHER = 2 };
@@ -722,10 +723,10 @@ struct ClusterGen {  // the leader's resumable walk over eligible candidates
 
 // Leader only: refill the candidate list when it is used up (the eligible
 // members among the next CL_NT above the stop level, in key order) and
-// publish the next batch of up to CL_CS * 32 untested candidates in C.blo /
+// publish the next batch of up to cs * 32 untested candidates in C.blo /
 // C.bn, or C.bend = 1 when none remain.  Every CTA of the cluster then tests
 // one candidate of the batch per warp.
-__device__ void leader_next_batch(const uint8_t* einel, int P, ClusterGen& G, ClusterCtl& C, SelShared& S) {
+__device__ void leader_next_batch(const uint8_t* einel, int P, ClusterGen& G, ClusterCtl& C, SelShared& S, int cs) {
   const int tid = threadIdx.x;
   while (G.pos >= G.m && G.c0 < P) {
     const int j = G.c0 + tid;
@@ -744,7 +745,7 @@ __device__ void leader_next_batch(const uint8_t* einel, int P, ClusterGen& G, Cl
   if (tid == 0) {
     C.bend = G.pos >= G.m;
     C.blo = G.pos;
-    C.bn = min(G.m - G.pos, CL_CS * 32);
+    C.bn = min(G.m - G.pos, cs * 32);
   }
 }
 
@@ -802,6 +803,7 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
                                       const PredConst& c, SelShared& S, ClusterCtl& C, int cap, int nb) {
   const int tid = threadIdx.x;
   const bool leader = cluster.block_rank() == 0;
+  const int cs = (int)cluster.num_blocks();
   ClusterCtl* LC = cluster.map_shared_rank(&C, 0);
   const float scale0 = c.bin_scale0 / (float)((n + nb - 2) / (nb - 1));
   // the first pass: threshold-count bins over every distance
@@ -856,7 +858,7 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
         for (int b = tid; b < NB; b += blockDim.x) {
           unsigned cn = S.cnt[b];
           unsigned long long mn = S.dmn[b], mx = S.dmx[b];
-          for (int r = 1; r < CL_CS; ++r) {
+          for (int r = 1; r < cs; ++r) {
             const SelShared* R = cluster.map_shared_rank(&S, r);
             cn += R->cnt[b];
             const unsigned long long a1 = R->dmn[b], a2 = R->dmx[b];
@@ -869,7 +871,7 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
         }
         if (first && tid == 0) {
           unsigned long long m = S.dmax_all;
-          for (int r = 1; r < CL_CS; ++r) {
+          for (int r = 1; r < cs; ++r) {
             const unsigned long long v = cluster.map_shared_rank(&S, r)->dmax_all;
             m = v > m ? v : m;
           }
@@ -909,7 +911,7 @@ __device__ long long cluster_r_search(cg::cluster_group& cluster, const int4* __
       cluster.sync();  // every CTA's list is complete
       if (leader) {
         int off = S.nlist;
-        for (int r = 1; r < CL_CS; ++r) {
+        for (int r = 1; r < cs; ++r) {
           const SelShared* R = cluster.map_shared_rank(&S, r);
           const int mr = R->nlist;
           for (int j = tid; j < mr; j += blockDim.x) S.list[off + j] = R->list[j];
@@ -962,11 +964,12 @@ __device__ __forceinline__ int cluster_walk(const LevelArgs& a, const uint32_t* 
   const int rank = (int)cluster.block_rank();
   const bool leader = rank == 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cs = (int)cluster.num_blocks();
   ClusterCtl* LC = cluster.map_shared_rank(&C, 0);
   ClusterGen* LG = cluster.map_shared_rank(&G, 0);
   int e = -1;
   while (true) {
-    if (leader) leader_next_batch(einel, C.P, G, C, S);
+    if (leader) leader_next_batch(einel, C.P, G, C, S, cs);
     cluster.sync();  // batch published
     if (LC->bend) break;
     const int blo = LC->blo, bn = LC->bn;
@@ -1003,7 +1006,7 @@ __device__ __forceinline__ int cluster_walk(const LevelArgs& a, const uint32_t* 
       cluster.sync();  // walk decision (or the shared test) published
       const int kc = LC->coop;
       if (kc < 0) break;
-      if (peak_part_beaten(a, egs[LG->list[kc]], glabel, rank * 32 + warp, CL_CS * 32) && lane == 0)
+      if (peak_part_beaten(a, egs[LG->list[kc]], glabel, rank * 32 + warp, cs * 32) && lane == 0)
         atomicExch(&LC->cbeat, 1);
       cluster.sync();  // every share of the shared test done
       if (leader && tid == 0) G.peak_of[kc] = (int8_t)(C.cbeat ? PEAK_NO : PEAK_YES);
@@ -1022,7 +1025,8 @@ __device__ void cluster_level(const LevelArgs& a, const int seg, SelShared& S, C
   const unsigned base = a.seg_off[seg];
   const int n = (int)(a.seg_off[seg + 1] - base);
   const int tid = threadIdx.x;
-  const int lo_r = (int)((long long)n * rank / CL_CS), hi_r = (int)((long long)n * (rank + 1) / CL_CS);
+  const int cs = (int)cluster.num_blocks();
+  const int lo_r = (int)((long long)n * rank / cs), hi_r = (int)((long long)n * (rank + 1) / cs);
   const int4* epos = a.epos + base;
   const long long* esig = a.esig + base;
   const uint32_t* egs = a.egs + base;
@@ -1103,23 +1107,26 @@ __device__ void cluster_level(const LevelArgs& a, const int seg, SelShared& S, C
 // on a count read back by the host.
 // ---------------------------------------------------------------------------
 struct TierQueue {
-  unsigned count[4];  // giant, large, small (from k_seg_sizes); [3] unused
-  unsigned next[4];   // fetch counters: giant, large, medium, small
+  unsigned count[4];  // giant (huge included), large, small, huge (from k_seg_sizes)
+  unsigned next[5];   // fetch counters: giant, large, medium, small, huge
   unsigned nseg;
 };
 
 // first index in the size-sorted order and count of bin t
 __device__ __forceinline__ void tier_range(const TierQueue& q, int t, unsigned& first, unsigned& cnt) {
-  const unsigned ng = q.count[0], nl = q.count[1], ns = q.count[2];
+  const unsigned ng = q.count[0], nl = q.count[1], ns = q.count[2], nh = q.count[3];
   const unsigned nm = q.nseg - ng - nl - ns;
-  if (t == 0) { first = 0; cnt = ng; }
+  if (t == 4) { first = 0; cnt = nh; }
+  else if (t == 0) { first = nh; cnt = ng - nh; }
   else if (t == 1) { first = ng; cnt = nl; }
   else if (t == 2) { first = ng + nl; cnt = nm; }
   else { first = q.nseg - ns; cnt = ns; }
 }
 
-__global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
-    k_level_cluster_q(LevelArgs a, const uint32_t* __restrict__ order, TierQueue* q) {
+// tier 0 (giants) on 8-CTA clusters, tier 4 (huge groups) on 16-CTA clusters
+template <int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(CL_NT)
+    k_level_cluster_q(LevelArgs a, const uint32_t* __restrict__ order, TierQueue* q, int tier) {
   __shared__ SelShared S;
   __shared__ ClusterCtl C;
   __shared__ ClusterGen G;
@@ -1127,9 +1134,9 @@ __global__ void __cluster_dims__(CL_CS, 1, 1) __launch_bounds__(CL_NT)
   cg::cluster_group cluster = cg::this_cluster();
   const bool leader = cluster.block_rank() == 0;
   unsigned first, cnt;
-  tier_range(*q, 0, first, cnt);
+  tier_range(*q, tier, first, cnt);
   for (;;) {
-    if (leader && threadIdx.x == 0) item = atomicAdd(&q->next[0], 1u);
+    if (leader && threadIdx.x == 0) item = atomicAdd(&q->next[tier], 1u);
     cluster.sync();
     const unsigned it = *cluster.map_shared_rank(&item, 0);
     cluster.sync();  // every CTA has read the leader's item before it changes
@@ -1281,7 +1288,7 @@ __global__ void __launch_bounds__(256) k_level_warp_q(LevelArgs a, const uint32_
 }
 
 // segment sizes as descending sort keys, and the size-bin counts
-__global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int giant, int large, int small,
+__global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int huge, int giant, int large, int small,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ val, unsigned* __restrict__ counts,
                             unsigned* __restrict__ nseg_out) {
   int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1290,6 +1297,7 @@ __global__ void k_seg_sizes(const uint32_t* __restrict__ seg_off, int nseg, int 
   const uint32_t sz = seg_off[g + 1] - seg_off[g];
   key[g] = 0xffffffffu - sz;
   val[g] = (uint32_t)g;
+  if (sz > (uint32_t)huge) atomicAdd(&counts[3], 1u);
   if (sz > (uint32_t)giant) atomicAdd(&counts[0], 1u);
   else if (sz > (uint32_t)large) atomicAdd(&counts[1], 1u);
   else if (sz <= (uint32_t)small) atomicAdd(&counts[2], 1u);
@@ -1335,10 +1343,23 @@ __global__ void k_level_halo_nuclei(const uint32_t* __restrict__ seg_off, int ns
 // resident blocks per SM of the persistent level kernels (same for every
 // device of one build; queried once)
 static std::atomic<int> g_occ_l{0}, g_occ_m{0}, g_occ_w{0};
+// 16-CTA clusters that can be resident at once (0: that size does not fit
+// this device, and huge groups stay on 8-CTA clusters)
+static std::atomic<int> g_cl16{0};
 
 void level_prepare() {
   if (g_occ_l.load()) return;
   int l = 0, m = 0, w = 0;
+  int c16 = 0;
+  if (cudaFuncSetAttribute(k_level_cluster_q<CL_HUGE_CS>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+      cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL_HUGE_CS, 1, 1);
+    cfg.blockDim = dim3(CL_NT, 1, 1);
+    if (cudaOccupancyMaxActiveClusters(&c16, k_level_cluster_q<CL_HUGE_CS>, &cfg) != cudaSuccess) c16 = 0;
+  }
+  cudaGetLastError();  // an unsupported size leaves only the answer 0
+  g_cl16.store(c16 > 0 ? c16 : 0);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l, k_level_q<1024>, 1024, 0) != cudaSuccess || l < 1) l = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_level_q<256>, 256, 0) != cudaSuccess || m < 1) m = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&w, k_level_warp_q, 256, 0) != cudaSuccess || w < 1) w = 1;
@@ -1356,8 +1377,8 @@ int level_run(const LevelArgs& a, cudaStream_t st) {
 }
 
 int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws, cudaStream_t st,
-                      cudaStream_t side, cudaStream_t side2, cudaEvent_t fork, cudaEvent_t join,
-                      cudaEvent_t join2, unsigned* host_counts) {
+                      cudaStream_t side, cudaStream_t side2, cudaStream_t side3, cudaEvent_t fork,
+                      cudaEvent_t join, cudaEvent_t join2, cudaEvent_t join3, unsigned* host_counts) {
   (void)host_counts;
   if (a.nseg <= 0) return CSO_OK;
   size_t mark = ws.off;
@@ -1371,15 +1392,19 @@ int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws
     return CSO_ERR_BUDGET;
   }
   CSO_CUDA(cudaMemsetAsync(q, 0, sizeof(TierQueue), st));
-  k_seg_sizes<<<CL(cdiv(a.nseg, 256)), 256, 0, st>>>(a.seg_off, a.nseg, sc.giant, sc.large(), sc.small, key, val,
-                                                     q->count, &q->nseg);
+  level_prepare();
+  const int c16 = g_cl16;
+  // groups above the huge bound (and the giant bound) run on 16-CTA clusters
+  // where the device holds them
+  const int huge = c16 > 0 ? std::max(sc.giant, sc.huge) : INT_MAX;
+  k_seg_sizes<<<CL(cdiv(a.nseg, 256)), 256, 0, st>>>(a.seg_off, a.nseg, huge, sc.giant, sc.large(), sc.small, key,
+                                                     val, q->count, &q->nseg);
   // largest groups first: giants start at once, the rest fill in behind them
   uint32_t *pk = key, *pv = val;
   CSO_TRY(radix_sort_32(&pk, &pv, key2, val2, a.nseg, 32, ws, st));
   CSO_CUDA(cudaGetLastError());
   // persistent grids sized to the device; blocks of a bin leave when its
   // queue is empty
-  level_prepare();
   const int occ_l = g_occ_l, occ_m = g_occ_m, occ_w = g_occ_w;
   const int sms = cso_sm_count();
   const int n_clusters = sms / CL_CS > 0 ? sms / CL_CS : 1;
@@ -1388,8 +1413,14 @@ int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws
   auto cap = [nseg](long long g) { return (unsigned)(g < nseg ? g : nseg); };
   CSO_CUDA(cudaEventRecord(fork, st));
   CSO_CUDA(cudaStreamWaitEvent(side, fork, 0));
-  k_level_cluster_q<<<CL(cap(n_clusters) * CL_CS), CL_NT, 0, side>>>(a, pv, q);
+  k_level_cluster_q<CL_CS><<<CL(cap(n_clusters) * CL_CS), CL_NT, 0, side>>>(a, pv, q, 0);
   CSO_CUDA(cudaGetLastError());
+  if (c16 > 0) {
+    // at most two: huge groups are few, and every 16-CTA cluster holds 16 SMs
+    CSO_CUDA(cudaStreamWaitEvent(side3, fork, 0));
+    k_level_cluster_q<CL_HUGE_CS><<<CL(cap(c16 < 2 ? c16 : 2) * CL_HUGE_CS), CL_NT, 0, side3>>>(a, pv, q, 4);
+    CSO_CUDA(cudaGetLastError());
+  }
   CSO_CUDA(cudaStreamWaitEvent(side2, fork, 0));
   k_level_q<1024><<<CL(cap((long long)sms * occ_l)), 1024, 0, side2>>>(a, pv, q, 1);
   k_level_q<256><<<CL(cap((long long)sms * occ_m)), 256, 0, st>>>(a, pv, q, 2);
@@ -1399,6 +1430,10 @@ int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws
   CSO_CUDA(cudaStreamWaitEvent(st, join, 0));
   CSO_CUDA(cudaEventRecord(join2, side2));
   CSO_CUDA(cudaStreamWaitEvent(st, join2, 0));
+  if (c16 > 0) {
+    CSO_CUDA(cudaEventRecord(join3, side3));
+    CSO_CUDA(cudaStreamWaitEvent(st, join3, 0));
+  }
   ws.off = mark;
   return CSO_OK;
 }

@@ -44,6 +44,10 @@ struct LevelArgs {
   int nb;                   // histogram bins (<= 1024)
 };
 
+// groups above this many members (and above the giant bound) run on 16-CTA
+// thread-block clusters where the device can hold one
+#define CSO_HUGE_GROUP (1 << 19)
+
 // size bins of the batched schedule: groups above `giant` members run on an
 // 8-CTA thread-block cluster, groups above large() on a 1024-thread block,
 // groups up to `small` members on one warp, the rest on a 256-thread block;
@@ -51,6 +55,7 @@ struct LevelArgs {
 struct LevelSchedule {
   int giant = 16384;
   int small = 64;
+  int huge = CSO_HUGE_GROUP;  // above max(huge, giant): 16-CTA clusters
   int large() const { return giant / 16 > 512 ? giant / 16 : 512; }
 };
 
@@ -59,8 +64,8 @@ int level_run(const LevelArgs& a, cudaStream_t st);
 // kept out of stream capture
 void level_prepare();
 int level_run_batched(const LevelArgs& a, const LevelSchedule& sc, Workspace& ws, cudaStream_t st,
-                      cudaStream_t side, cudaStream_t side2, cudaEvent_t fork, cudaEvent_t join,
-                      cudaEvent_t join2, unsigned* host_counts);
+                      cudaStream_t side, cudaStream_t side2, cudaStream_t side3, cudaEvent_t fork,
+                      cudaEvent_t join, cudaEvent_t join2, cudaEvent_t join3, unsigned* host_counts);
 // ehalo[j] = global halo of member j (hbase[g] + its nucleus ordinal, or -1)
 // and the nucleus records of every halo; n_members = seg_off[nseg] and
 // n_halos = hbase[nseg] as the host knows them (launch sizes)

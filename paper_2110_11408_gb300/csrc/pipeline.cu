@@ -404,10 +404,12 @@ int readback(cso_ctx* c, const void* dev, size_t bytes) {
 int level_stage(cso_ctx* c, const LevelArgs& L, const LevelSchedule& sched, unsigned* host_counts) {
   cudaStream_t st = c->stream;
   if (!(c->flags & CSO_FLAG_GRAPH))
-    return level_run_batched(L, sched, c->ws, st, c->side, c->side2, c->fork, c->join, c->join2, host_counts);
+    return level_run_batched(L, sched, c->ws, st, c->side, c->side2, c->side3, c->fork, c->join, c->join2, c->join3,
+                             host_counts);
   for (int i = 0; i < CSO_LEVEL_GRAPHS; ++i) {
     LevelGraph& G = c->graphs[i];
-    if (G.exec && G.giant == sched.giant && G.small == sched.small && !memcmp(&G.args, &L, sizeof(LevelArgs))) {
+    if (G.exec && G.giant == sched.giant && G.small == sched.small && G.huge == sched.huge &&
+        !memcmp(&G.args, &L, sizeof(LevelArgs))) {
       ++c->graph_hits;
       CSO_CUDA(cudaGraphLaunch(G.exec, st));
       return CSO_OK;
@@ -417,7 +419,8 @@ int level_stage(cso_ctx* c, const LevelArgs& L, const LevelSchedule& sched, unsi
   // keep issuing work) and keep it in the oldest slot
   level_prepare();
   CSO_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  const int rc = level_run_batched(L, sched, c->ws, st, c->side, c->side2, c->fork, c->join, c->join2, host_counts);
+  const int rc = level_run_batched(L, sched, c->ws, st, c->side, c->side2, c->side3, c->fork, c->join, c->join2,
+                                   c->join3, host_counts);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(st, &graph);
   if (rc != CSO_OK) {
@@ -437,6 +440,7 @@ int level_stage(cso_ctx* c, const LevelArgs& L, const LevelSchedule& sched, unsi
   memcpy(&G.args, &L, sizeof(LevelArgs));
   G.giant = sched.giant;
   G.small = sched.small;
+  G.huge = sched.huge;
   ++c->graph_captures;
   CSO_CUDA(cudaGraphLaunch(G.exec, st));
   return CSO_OK;

@@ -27,7 +27,7 @@ struct ServedState;
 // arguments (the same box gives the same workspace offsets, hence the key)
 struct LevelGraph {
   LevelArgs args;
-  int giant = 0, small = 0;
+  int giant = 0, small = 0, huge = 0;
   cudaGraphExec_t exec = nullptr;
 };
 #define CSO_LEVEL_GRAPHS 4
@@ -37,7 +37,8 @@ struct cso_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;   // second stream of the batched schedule (giant groups)
   cudaStream_t side2 = nullptr;  // third stream (large groups)
-  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr;
+  cudaStream_t side3 = nullptr;  // fourth stream (huge groups on 16-CTA clusters)
+  cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr, join3 = nullptr;
   size_t budget = 0;
   uint32_t flags = 0;
   Workspace ws;

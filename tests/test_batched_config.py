@@ -26,24 +26,28 @@ def gpu():
     return True
 
 
-def run(flags, pos, ids, p, giant=None, small=64):
+def run(flags, pos, ids, p, giant=None, small=64, huge=None):
     with cso.Context(0, flags=flags) as c:
         if giant:
             cso.cso_set_schedule(c.h, giant, small)
+        if huge:
+            cso.cso_set_huge_group(c.h, huge)
         return c.find_groups(pos, ids, p)
 
 
 def test_batched_recipe_at_one_tenth_full_parity(gpu):
     """400k particles, a 2e5 giant: the plain schedule and the batched one
-    with clusters above 16,384 and above 2,048 members, all equal to the
-    oracle."""
+    with clusters above 16,384 and above 2,048 members, and with 16-CTA
+    clusters above 16,384, all equal to the oracle."""
     pos, ids, meta = synth.batched(total=400_000, giant=200_000)
     p = cso.cso_params_default(meta["u"])
     a = run(0, pos, ids, p)
     o = assert_matches_oracle(a, pos, ids, meta["u"])
     assert o["stats"]["l0_groups"] > 500
-    for giant in (16384, 2048):
-        b = run(cso.FLAG_BATCHED, pos, ids, p, giant=giant)
+    # clusters above 16,384 and above 2,048 members; then the giant (and
+    # every group above 16,384) on 16-CTA clusters
+    for giant, huge in ((16384, None), (2048, None), (2048, 16384)):
+        b = run(cso.FLAG_BATCHED, pos, ids, p, giant=giant, huge=huge)
         for k in ("sigma", "l0", "l1", "l2"):
             assert np.array_equal(a[k], b[k]), k
         assert np.array_equal(a["halos"], b["halos"])

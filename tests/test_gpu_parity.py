@@ -422,6 +422,22 @@ def test_cluster_path_for_every_group_above_64():
         c.close()
 
 
+def test_huge_cluster_path_for_every_group_above_64():
+    """Giant and huge thresholds 64: every group above 64 members runs on a
+    16-CTA thread-block cluster (a non-portable size; 8-CTA clusters where
+    the device cannot hold one), plain and under select stress."""
+    for flags in (cso.FLAG_BATCHED, cso.FLAG_BATCHED | cso.FLAG_SELECT_STRESS):
+        c = cso.Context(0, flags=flags)
+        try:
+            cso.cso_set_schedule(c.h, 64, 64)
+            cso.cso_set_huge_group(c.h, 64)
+            pos, ids, meta = synth.tiny()
+            g, o = run_both(c, pos, ids)
+            assert_same(g, o)
+        finally:
+            c.close()
+
+
 def test_cluster_path_select_stress():
     c = cso.Context(0, flags=cso.FLAG_BATCHED | cso.FLAG_SELECT_STRESS)
     try:
