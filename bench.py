@@ -44,7 +44,7 @@ OPS_PER_PAIR = 11  # 3 sub, 3 mul, 2 add for d; compare; b2 - d; accumulate
 # DRAM bytes (read + write) of one k_density launch per workload, from the
 # single-pass ncu capture summarised in profiles/ (only for the kernel as it
 # stands; absent workloads report null)
-DENSITY_DRAM_BYTES = {"medium": 3.2497e9}
+DENSITY_DRAM_BYTES = {"medium": 3.2425e9}
 
 
 def cell_table_bytes(u):
