@@ -208,7 +208,9 @@ int cso_params_derive(cso_params* p);
 int cso_params_cosmology(cso_params* p, double omega_m0, double z);
 
 /* Run the whole hot path on one periodic box: kernel density, L0, L1, L2,
- * labels and catalogue.  Synchronous: returns after the outputs are written. */
+ * labels and catalogue.  Synchronous: returns after the outputs are written
+ * (and, on an error return, with no copy into them still in flight; their
+ * contents are then unspecified). */
 int cso_find_groups(cso_ctx* ctx, const cso_input* in, const cso_params* p, cso_output* out);
 
 /* Served path (continuous batching).  Queue a box and return a ticket at

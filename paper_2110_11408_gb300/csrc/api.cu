@@ -151,6 +151,9 @@ extern "C" int cso_init(cso_ctx** out, int device, size_t budget, uint32_t flags
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side3, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join3, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->out_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->out_copied, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, sizeof(long long) * 64);
   for (int i = 0; e == cudaSuccess && i <= CSO_MAX_STAGES; ++i) e = cudaEventCreate(&c->ev[i]);
   if (e != cudaSuccess) {
@@ -180,6 +183,10 @@ extern "C" void cso_free(cso_ctx* c) {
   if (c->side2) cudaStreamDestroy(c->side2);
   if (c->join3) cudaEventDestroy(c->join3);
   if (c->side3) cudaStreamDestroy(c->side3);
+  if (c->copy) cudaStreamSynchronize(c->copy);
+  if (c->out_ready) cudaEventDestroy(c->out_ready);
+  if (c->out_copied) cudaEventDestroy(c->out_copied);
+  if (c->copy) cudaStreamDestroy(c->copy);
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);

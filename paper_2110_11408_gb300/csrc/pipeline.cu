@@ -836,6 +836,28 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   }
   if (ol1) k_fill_u64<<<G1(n)>>>(ol1, n, NONE);
   if (ol2) k_fill_u64<<<G1(n)>>>(ol2, n, NONE);
+  // kernel sums and L0 labels are final here: write them in input order now,
+  // and with host outputs copy them back on the copy stream while the group
+  // stages run
+  k_out_cells<<<G1(n)>>>(inv, N, sigma, root, minid, osig, ol0);
+  CSO_CUDA(cudaGetLastError());
+  const bool early_copy = host_out && (out->l0 || out->sigma);
+  // every return from here on (errors included) leaves no copy in flight into
+  // the caller's buffers
+  struct CopyWait {
+    cudaStream_t s;
+    bool on;
+    ~CopyWait() {
+      if (on) cudaStreamSynchronize(s);
+    }
+  } copy_wait{c->copy, early_copy};
+  if (early_copy) {
+    CSO_CUDA(cudaEventRecord(c->out_ready, st));
+    CSO_CUDA(cudaStreamWaitEvent(c->copy, c->out_ready, 0));
+    if (out->l0) CSO_CUDA(cudaMemcpyAsync(out->l0, ol0, 8 * n, cudaMemcpyDeviceToHost, c->copy));
+    if (out->sigma) CSO_CUDA(cudaMemcpyAsync(out->sigma, osig, 8 * n, cudaMemcpyDeviceToHost, c->copy));
+    CSO_CUDA(cudaEventRecord(c->out_copied, c->copy));
+  }
 
   GroupsIn gin{&g, spos, sigma, sid, root, minid, nullptr, N, 0};
   int nrows = 0;
@@ -851,8 +873,6 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
     c->stats[6] = (int64_t)hm2.pairs;
   }
   S.mark("output");
-  k_out_cells<<<G1(n)>>>(inv, N, sigma, root, minid, osig, ol0);
-  CSO_CUDA(cudaGetLastError());
   out->n_halos = nrows;
   c->stats[5] = nrows;
   const int ncopy = nrows <= out->halo_cap ? nrows : 0;
@@ -866,11 +886,10 @@ int pipeline_run(cso_ctx* c, const cso_input* in, const cso_params* p, cso_outpu
   // ---- d2h ----
   S.mark("d2h");
   if (host_out) {
-    if (out->l0) CSO_CUDA(cudaMemcpyAsync(out->l0, ol0, 8 * n, cudaMemcpyDeviceToHost, st));
     if (out->l1) CSO_CUDA(cudaMemcpyAsync(out->l1, ol1, 8 * n, cudaMemcpyDeviceToHost, st));
     if (out->l2) CSO_CUDA(cudaMemcpyAsync(out->l2, ol2, 8 * n, cudaMemcpyDeviceToHost, st));
-    if (out->sigma) CSO_CUDA(cudaMemcpyAsync(out->sigma, osig, 8 * n, cudaMemcpyDeviceToHost, st));
   }
+  if (early_copy) CSO_CUDA(cudaStreamWaitEvent(st, c->out_copied, 0));
   S.finish();
   CSO_CUDA(cudaMemcpyAsync(c->pinned, meta, sizeof(Meta), cudaMemcpyDeviceToHost, st));
   CSO_CUDA(cudaStreamSynchronize(st));

@@ -38,7 +38,9 @@ struct cso_ctx {
   cudaStream_t side = nullptr;   // second stream of the batched schedule (giant groups)
   cudaStream_t side2 = nullptr;  // third stream (large groups)
   cudaStream_t side3 = nullptr;  // fourth stream (huge groups on 16-CTA clusters)
+  cudaStream_t copy = nullptr;   // device-to-host copies of outputs final before the step ends
   cudaEvent_t fork = nullptr, join = nullptr, join2 = nullptr, join3 = nullptr;
+  cudaEvent_t out_ready = nullptr, out_copied = nullptr;
   size_t budget = 0;
   uint32_t flags = 0;
   Workspace ws;
