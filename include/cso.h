@@ -46,10 +46,11 @@ extern "C" {
 
 /* context flags (cso_init) */
 #define CSO_FLAG_BATCHED 1u /* CompaSO levels by group size: warp, 256- and 1024-thread blocks, 8-CTA clusters,
-                              largest first, on three concurrent streams */
+                              16-CTA clusters for huge groups (cso_set_huge_group), largest first, on four
+                              concurrent streams */
 #define CSO_FLAG_TIMING 2u  /* record per-stage CUDA events (cso_stage_times) */
 /* with CSO_FLAG_BATCHED: each CompaSO level stage (size sort, work queue and
- * the four persistent tier kernels) is captured once as a CUDA graph and
+ * the five persistent tier kernels) is captured once as a CUDA graph and
  * replayed by later calls with identical launch arguments (a box of the same
  * shape in the same context); the rest of the step is launched directly (its
  * launch sizes are read back from the device between stages) */

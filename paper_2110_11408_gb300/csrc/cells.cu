@@ -1,9 +1,10 @@
 // Cell binning, kernel density and L0 friends-of-friends.
 //
 // Particles are binned into nc^3 cells of side 2^21/nc >= b (a counting sort
-// into a dense cell table, x fastest), so every neighbour within b of a
-// particle lies in the 27 cells around its own and, for the three cells of
-// one (y, z) row, in one contiguous run of the sorted array.  Periodic wrap
+// into a dense cell table, x fastest, each cell ordered by x inside), so
+// every neighbour within b of a particle lies in the 27 cells around its own
+// and, for the three cells of one (y, z) row, in one contiguous run of the
+// sorted array, itself sorted by x.  Periodic wrap
 // is handled per run by shifting the query point by one box length, never
 // per pair.  With side <= 2^14 grid units every |dx| inside the stencil is
 // below 2^15, so squared distances fit uint32 exactly.
