@@ -354,7 +354,7 @@ __device__ __forceinline__ void run_bounds(const WarpRows& R, int r, uint32_t& l
 }
 
 template <bool SMALL>
-__global__ void __launch_bounds__(DENS_WARPS * 32, 4) k_density(CellGrid g, const int4* __restrict__ spos, int n,
+__global__ void __launch_bounds__(DENS_WARPS * 32, 5) k_density(CellGrid g, const int4* __restrict__ spos, int n,
                                                                  uint32_t b2, int reach, int include_self,
                                                                  long long* __restrict__ sigma,
                                                                  const uint8_t* __restrict__ only,
