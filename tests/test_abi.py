@@ -79,3 +79,12 @@ def test_probe_rejects_a_short_result_buffer():
     out = (ctypes.c_double * 2)()
     assert cso.lib().cso_probe_peaks(0, out, 2) == cso.CSO_ERR_ARG
     assert b"3 results" in cso.lib().cso_last_error()
+
+
+def test_schedule_setters_check_their_arguments():
+    # argument checks come before any context use, so these run without a GPU
+    L = cso.lib()
+    assert L.cso_set_schedule(None, 32, 64) == cso.CSO_ERR_ARG
+    assert L.cso_set_schedule(None, 16384, 0) == cso.CSO_ERR_ARG
+    assert L.cso_set_huge_group(None, 1 << 19) == cso.CSO_ERR_ARG
+    assert L.cso_set_huge_group(None, 63) == cso.CSO_ERR_ARG
